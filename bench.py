@@ -1,0 +1,404 @@
+#!/usr/bin/env python3
+"""Throughput benchmark of brute-force dedispersion on GB300.
+
+One step = one forward dedispersion of the survey-scale workload (1 beam,
+1024 channels over 1420-1720 MHz, 50 us sampling, 2048 trial DMs 0-511.75,
+20000 output samples, FP32 input, unit weights, 10 injected pulses) through
+the C ABI's dd_execute. Prints ONE JSON line (rank 0).
+
+  value     DM-trial*samples/s over the whole job (beams are independent:
+            every rank dedisperses its own beam, weak scaling)
+  e2e       the same metric through dd_execute_host: pinned host input ->
+            device -> kernel -> host output, every step
+  roofline  the forward kernel against the FP32 ALU peak (it is issue/ALU
+            bound: ~150 adds per compulsory HBM byte), plus its HBM fraction
+  extras    8-bit / FP16 batched forms of the uneven-beam workload against
+            plain FP32 launches of the same workload, the HBM-bound 96-beam
+            FP32 point, and the differentiable workload's forward+backward
+
+--impl reference times the FP64 CPU oracle on a bounded sample of the same
+workload (the paper publishes no code to run).
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "DM-trial·samples/s"
+UNIT = "DM-trial·samples/s"
+WORKLOAD = "cfg2"
+L2_FLUSH_BYTES = 256 << 20
+
+
+def _args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-extras", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--tune-ms", type=int, default=0,
+                    help="auto-tune the forward variant for this budget first (0 = no)")
+    return ap.parse_args()
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except OSError:
+        return {"hbm_gbs": 6800.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+# ---------------------------------------------------------------- clocks
+
+class ClockSampler:
+    """nvidia-smi clock / throttle samples taken while the timed region runs."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, uuid):
+        self.uuid = uuid
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            cmd = ["nvidia-smi", "--query-gpu=" + self.Q, "--format=csv,noheader,nounits",
+                   "-lms", "50"]
+            if self.uuid:
+                cmd += ["-i", self.uuid]
+            self.proc = subprocess.Popen(cmd, stdout=open(self.path, "w"),
+                                         stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        rows = []
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) >= 9:
+                rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return None
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({n for r in rows for n, v in zip(names, r[5:9]) if v == "Active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": float(rows[0][2]) if rows[0][2].replace(".", "").isdigit() else None,
+                "reasons": reasons, "samples": len(rows),
+                "power_w_max": max(float(r[3]) for r in rows
+                                   if r[3].replace(".", "").isdigit()) if rows else None}
+
+
+# ---------------------------------------------------------------- helpers
+
+def _setup_inputs(s, shifts, seed, dtype="f32", n_pulses=10):
+    import synth
+    pulses = synth.pulse_plan(s, seed, n_per_beam=n_pulses)
+    return synth.make_input(s.with_(dtype=dtype), shifts, seed=seed, pulses=pulses,
+                            pad_value={"u8": np.uint8(0), "bf16": np.uint16(0)}.get(dtype, 0))
+
+
+def _time_steps(fn, steps, warmup, flush, torch):
+    """Per-step CUDA-event times (ms) of fn() on the current stream, with the
+    L2 flushed (a 256 MB write) before every step, outside the events."""
+    for _ in range(warmup):
+        flush.zero_()
+        fn()
+    torch.cuda.synchronize()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(steps)]
+    for e0, e1 in ev:
+        flush.zero_()
+        e0.record()
+        fn()
+        e1.record()
+    torch.cuda.synchronize()
+    return [e0.elapsed_time(e1) for e0, e1 in ev]
+
+
+def _cpu_baseline(x, w, shifts, s, target_s=12.0):
+    """The FP64 oracle on the first n trial DMs (all channels, all samples),
+    n doubled until one run takes >= target_s or covers every trial."""
+    import oracle
+    n = 4
+    while True:
+        t0 = time.perf_counter()
+        oracle.forward(x, w, shifts[:n], s.n_out)
+        dt = time.perf_counter() - t0
+        if dt >= target_s or n >= s.n_dm:
+            break
+        n = min(s.n_dm, n * 2 if dt < target_s / 4 else max(n + 1, int(n * target_s / dt)))
+    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    return {"value": n * s.n_out * s.batch / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": "FP64 oracle (C, OpenMP over outputs) on trial DMs [0, %d) of %d, all %d "
+                      "channels and %d samples, one beam: %.1f s" % (n, s.n_dm, s.n_chan,
+                                                                   s.n_out, dt)}
+
+
+# ---------------------------------------------------------------- reference arm
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    import oracle
+    import synth
+    s = synth.setup(WORKLOAD)
+    sh = oracle.shift_table(s.freqs(), s.f_ref, s.t_samp, s.dms())
+    x = _setup_inputs(s, sh, seed=2)
+    w = np.ones(s.n_chan, np.float32)
+    budget = 150.0 / max(1, args.steps + args.warmup)  # seconds per step
+    n = 1
+    while n < s.n_dm:
+        t0 = time.perf_counter()
+        oracle.forward(x, w, sh[:n], s.n_out)
+        if time.perf_counter() - t0 > budget / 2:
+            break
+        n *= 2
+    for _ in range(args.warmup):
+        oracle.forward(x, w, sh[:n], s.n_out)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        oracle.forward(x, w, sh[:n], s.n_out)
+    dt = (time.perf_counter() - t0) / max(1, args.steps)
+    v = n * s.n_out / dt
+    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT,
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": dt * 1e3, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "survey scale, 1 beam x 1024 ch x 2048 DM x 20000 samples "
+                                   "(sampled: trial DMs [0, %d))" % n},
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": "FP64 oracle on trial DMs [0, %d) of %d per step" % (n, s.n_dm)},
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ---------------------------------------------------------------- our arm
+
+def _extras(torch, flush, peaks, steps):
+    """Secondary measurement points (rank 0, one GPU)."""
+    import synth
+    from paper_1601_05052_gb300 import Batch, Plan, dedisperse
+    out = {}
+    g = torch.Generator(device="cuda")
+    n_rep = max(3, min(20, steps // 10))
+
+    def rand_input(p, seed, dtype):
+        g.manual_seed(seed)
+        xf = torch.randn(p.in_shape, generator=g, device="cuda", dtype=torch.float32)
+        if dtype == "u8":
+            return (128.0 + 16.0 * xf).round_().clamp_(0, 255).to(torch.uint8)
+        return xf.to({"f32": torch.float32, "f16": torch.float16, "bf16": torch.bfloat16}[dtype])
+
+    # uneven-beam batch: 96 x (64 ch) + 32 x (256 ch, low frequency)
+    hi, lo = synth.setup("cfg4_hi"), synth.setup("cfg4_lo")
+    units = hi.batch * hi.n_dm * hi.n_out + lo.batch * lo.n_dm * lo.n_out
+    res = {}
+    for dtype in ("u8", "f16", "f32"):
+        plans = [Plan.from_setup(s, dtype=dtype) for s in (hi, lo)]
+        xs = [rand_input(p, 40 + i, dtype) for i, p in enumerate(plans)]
+        ws = [torch.ones(p.n_chan, dtype=p.w_dtype, device="cuda") for p in plans]
+        outs = [torch.empty(p.out_shape, dtype=p.out_dtype, device="cuda") for p in plans]
+        if dtype == "f32":  # the plain form: one dd_execute launch per setup
+            fn = lambda: [p.execute(x, w, o) for p, x, w, o in zip(plans, xs, ws, outs)]
+        else:
+            bt = Batch(plans)
+            bt.tune(budget_ms=15000)
+            fn = lambda bt=bt: bt.execute(xs, ws, outs)
+        t = statistics.median(_time_steps(fn, n_rep, 2, flush, torch))
+        res[dtype] = units / (t * 1e-3)
+        del xs, outs
+        torch.cuda.empty_cache()
+    out["uneven_beams"] = {
+        "workload": "96 beams x (64 ch, 64 DM, 4096 samples) + 32 beams x (256 ch 120-180 MHz, "
+                    "2000 DM, 10000 samples)",
+        "batched_u8_graph": res["u8"], "batched_f16_graph": res["f16"],
+        "plain_f32_launches": res["f32"],
+        "speedup_u8_vs_f32": res["u8"] / res["f32"], "speedup_f16_vs_f32": res["f16"] / res["f32"],
+        "unit": UNIT}
+
+    # HBM-bound point: 96 beams of the 64-channel setup in FP32
+    s = synth.setup("cfg1x96")
+    p = Plan.from_setup(s)
+    x = rand_input(p, 7, "f32")
+    w = torch.ones(p.n_chan, device="cuda")
+    o = torch.empty(p.out_shape, device="cuda")
+    t = statistics.median(_time_steps(lambda: p.execute(x, w, o), n_rep, 2, flush, torch))
+    comp = (x.numel() * 4 + o.numel() * 4) / (t * 1e-3) / 1e9
+    out["f32_96beams_64ch"] = {"value": s.batch * s.n_dm * s.n_out / (t * 1e-3), "unit": UNIT,
+                               "ms": t, "effective_hbm_gbs": comp,
+                               "hbm_frac": comp / peaks["hbm_gbs"]}
+    del x, o
+
+    # differentiable workload: forward + backward (grad_in and grad_w)
+    s = synth.setup("cfg5")
+    p = Plan.from_setup(s)
+    x = rand_input(p, 9, "f32").requires_grad_(True)
+    w = torch.ones(p.n_chan, device="cuda", requires_grad=True)
+
+    def fwd_bwd():
+        y = dedisperse(p, x, w)
+        (y[:, 256:768, 2048:6144] ** 2).sum().backward()
+
+    tf = statistics.median(_time_steps(lambda: p.execute(x.detach(), w.detach()), n_rep, 2, flush,
+                                       torch))
+    tb = statistics.median(_time_steps(fwd_bwd, n_rep, 2, flush, torch))
+    units = s.batch * s.n_dm * s.n_out
+    out["differentiable_16beams"] = {"forward": units / (tf * 1e-3),
+                                     "forward_backward": units / (tb * 1e-3), "unit": UNIT,
+                                     "forward_ms": tf, "forward_backward_ms": tb}
+    return out
+
+
+def run_ours(args):
+    import torch
+    import torch.distributed as dist
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    else:
+        torch.cuda.set_device(0)
+
+    import synth
+    from paper_1601_05052_gb300 import Plan
+
+    peaks, peaks_kind = _peaks()
+    s = synth.setup(WORKLOAD)
+    plan = Plan.from_setup(s)
+    tune_rep = plan.tune(budget_ms=args.tune_ms) if args.tune_ms > 0 else None
+    sh = plan.shifts()
+    x_host = _setup_inputs(s, sh, seed=2 + rank)
+    w_host = np.ones(s.n_chan, np.float32)
+    x = torch.from_numpy(x_host).cuda()
+    w = torch.from_numpy(w_host).cuda()
+    out = torch.empty(plan.out_shape, dtype=torch.float32, device="cuda")
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+    props = torch.cuda.get_device_properties(torch.cuda.current_device())
+    uuid = getattr(props, "uuid", None)
+    uuid = ("GPU-" + str(uuid)) if uuid is not None and not str(uuid).startswith("GPU-") else uuid
+
+    step = lambda: plan.execute(x, w, out)
+    for _ in range(max(3, args.warmup)):
+        flush.zero_()
+        step()
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    clk = ClockSampler(uuid)
+    clk.start()
+    times = _time_steps(step, args.steps, 0, flush, torch)
+    clocks = clk.stop()
+    if world > 1:
+        dist.barrier()
+    total_ms = float(sum(times))
+    if world > 1:
+        t = torch.tensor([total_ms], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    ms = total_ms / args.steps
+    units = s.batch * s.n_dm * s.n_out
+    value = world * units / (ms * 1e-3)
+
+    # parity spot check of what was timed (sampled against nothing but itself
+    # is meaningless: the oracle parity lives in tests/; here only sanity)
+    plan.check_device()
+
+    # roofline of the forward kernel: one FP32 FMA per channel per output
+    ops = s.batch * s.n_dm * s.n_out * s.n_chan
+    n_sm = props.multi_processor_count
+    alu_peak = n_sm * 128 * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
+    achieved = ops / (ms * 1e-3) / 1e12
+    comp_bytes = x.numel() * 4 + out.numel() * 4
+    eff_gbs = comp_bytes / (ms * 1e-3) / 1e9
+
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic",
+            "config": {"workload": "survey scale: 1 beam x 1024 ch (1420-1720 MHz) x 2048 trial "
+                                   "DMs (0-511.75) x 20000 samples, FP32, unit weights, "
+                                   "10 pulses; per rank",
+                       "beams_per_rank": s.batch, "n_chan": s.n_chan, "n_dm": s.n_dm,
+                       "n_out": s.n_out, "input_len": plan.input_len,
+                       "l2": "flushed before every step (256 MB write outside the timed events)",
+                       "variant": plan.variant},
+            "roofline": {"bound": "alu", "achieved": achieved, "peak": alu_peak,
+                         "unit": "TFLOP/s", "frac": achieved / alu_peak, "traffic": None,
+                         "peak_kind": "derived: %d SMs x 128 FP32 lanes x %.0f MHz (%s max clock)"
+                                      % (n_sm, peaks.get("sm_max_mhz", 2070.0), peaks_kind),
+                         "op": "one FP32 add/FMA per channel per output (the paper's flop)",
+                         "hbm": {"effective_gbs": eff_gbs, "peak_gbs": peaks["hbm_gbs"],
+                                 "frac": eff_gbs / peaks["hbm_gbs"],
+                                 "compulsory_bytes": comp_bytes}},
+            "gpu_launches": args.steps,
+            "clocks": clocks}
+    if tune_rep:
+        line["tune"] = tune_rep
+
+    if rank == 0:
+        # end to end through the C ABI with pinned host buffers
+        hx = torch.from_numpy(x_host).pin_memory()
+        hw = torch.from_numpy(w_host).pin_memory()
+        hout = torch.empty(plan.out_shape, dtype=torch.float32).pin_memory()
+        n_e2e = max(3, min(args.steps, 20))
+        plan.execute_host(hx, hw, hout)
+        t0 = time.perf_counter()
+        for _ in range(n_e2e):
+            plan.execute_host(hx, hw, hout)
+        dt = (time.perf_counter() - t0) / n_e2e
+        line["e2e"] = {"value": world * units / dt, "unit": UNIT,
+                       "h2d_bytes_per_step": hx.numel() * 4 + hw.numel() * 4,
+                       "d2h_bytes_per_step": hout.numel() * 4, "ms_per_step": dt * 1e3}
+        line["paper_context"] = {"hd7970_2000dm_apertif_s": 0.106,
+                                 "hd7970_dm_trial_samples_per_s": 2000 * 20000 / 0.106,
+                                 "note": "AMD HD7970, OpenCL FP32, 2000 DMs (not 2048): context"}
+        if world == 1 and not args.no_extras:
+            line["extras"] = _extras(torch, flush, peaks, args.steps)
+        if world == 1 and not args.no_cpu_baseline:
+            line["cpu_baseline"] = _cpu_baseline(x_host, w_host, sh.astype(np.int64), s)
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.barrier()
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    args = _args()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -53,6 +53,7 @@ def _load():
         _lib.oracle_grad_w_f64.argtypes = [i32, i32, i32, i64, i64, P, P, P, P]
         _lib.oracle_adjoint_points_f64.argtypes = [i32, i32, i64, P, P, P, i64, P, P, P, P, P]
         _lib.oracle_grad_w_channels_f64.argtypes = [i32, i32, i32, i64, i64, P, P, P, i64, P, P, P]
+        _lib.oracle_forward_points_u8.argtypes = [i32, i64, P, i64, P, P, i64, P, P, P, P]
     return _lib
 
 
@@ -127,6 +128,20 @@ def forward_points(x: np.ndarray, w: np.ndarray, shifts: np.ndarray, pb, pd, pt,
     lib.oracle_forward_points_f64(C, stride, _p(xd), C * stride, _p(wd), _p(sh), pb.size,
                                   _p(pb), _p(pd), _p(pt), _p(out), _p(ab))
     return out, ab
+
+
+def forward_points_u8(x: np.ndarray, wq: np.ndarray, shifts: np.ndarray, pb, pd, pt):
+    """Exact int64 forward of 8-bit input at the points (pb[i], pd[i], pt[i])."""
+    lib = _load()
+    xu = np.ascontiguousarray(x, dtype=np.uint8)
+    B, C, stride = xu.shape
+    sh = np.ascontiguousarray(shifts, dtype=np.int64)
+    wq64 = np.ascontiguousarray(wq, dtype=np.int64)
+    pb, pd, pt = (np.ascontiguousarray(a, dtype=np.int64) for a in (pb, pd, pt))
+    out = np.empty(pb.size, dtype=np.int64)
+    lib.oracle_forward_points_u8(C, stride, _p(xu), C * stride, _p(wq64), _p(sh), pb.size,
+                                 _p(pb), _p(pd), _p(pt), _p(out))
+    return out
 
 
 def adjoint(g: np.ndarray, w: np.ndarray, shifts: np.ndarray, stride: int) -> np.ndarray:

@@ -220,3 +220,22 @@ void oracle_grad_w_channels_f64(int batch, int n_chan, int n_dm, int64_t n_out,
         if (absum) absum[i] = aacc;
     }
 }
+
+/* 8-bit forward at selected output points, exact in int64. */
+void oracle_forward_points_u8(int n_chan, int64_t stride, const uint8_t *in_b0,
+                              int64_t batch_elems, const int64_t *wq,
+                              const int64_t *shift, int64_t n_points,
+                              const int64_t *pb, const int64_t *pd,
+                              const int64_t *pt, int64_t *out)
+{
+    #pragma omp parallel for schedule(static)
+    for (int64_t i = 0; i < n_points; ++i) {
+        int64_t acc = 0;
+        const uint8_t *row0 = in_b0 + pb[i] * batch_elems;
+        for (int c = 0; c < n_chan; ++c) {
+            int64_t k = shift[pd[i] * n_chan + c];
+            acc += wq[c] * (int64_t)row0[(int64_t)c * stride + pt[i] + k];
+        }
+        out[i] = acc;
+    }
+}

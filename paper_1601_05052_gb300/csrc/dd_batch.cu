@@ -1,0 +1,441 @@
+// dd_batch.cu -- many beams of several observation setups in ONE persistent
+// kernel launch, replayed from a CUDA graph.
+//
+// The paper dedisperses one beam per call and notes that beams are
+// independent (Sections II and III-A). Here a batch groups plans of
+// different shapes (channels, trial DMs, samples, beams); the work items are
+// all (plan, beam, DM tile, time tile) tiles, numbered plan by plan with the
+// DM tile fastest. A persistent grid (resident CTAs only) pulls items from a
+// device counter with atomicAdd, so uneven setups balance across SMs; plans
+// are ordered heaviest tile first so the tail is made of light tiles. Every
+// plan in a batch uses one common kernel variant (one block shape, register
+// tile and staging depth: a launch has a single register and shared-memory
+// budget), with its own staging tables for that variant. The counter reset
+// and the launch form a two-node CUDA graph, re-parameterised only when the
+// buffer pointers change.
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <vector>
+
+#include "dd_fwd_tile.cuh"
+#include "dd_internal.h"
+
+namespace dd {
+
+constexpr int kMaxBatchPlans = 16;
+
+struct BatchArgs {
+    const FwdArgs *args;  // [n], device
+    int n, stages;
+    long long item_start[kMaxBatchPlans + 1];
+    unsigned long long *counter;
+};
+
+template <typename T, int DPT, int SPT>
+__global__ void __launch_bounds__(256, 1) dd_fwd_persistent_kernel(const BatchArgs ba) {
+    extern __shared__ __align__(128) unsigned char smem[];
+    __shared__ long long s_item;
+    uint64_t *full = reinterpret_cast<uint64_t *>(smem);
+    fwd_init_barriers(full, ba.stages);
+    uint32_t kbase = 0;
+    const long long n_items = ba.item_start[ba.n];
+    for (;;) {
+        if (threadIdx.x == 0) s_item = (long long)atomicAdd(ba.counter, 1ull);
+        __syncthreads();
+        const long long item = s_item;
+        if (item >= n_items) break;
+        int i = 0;
+        while (item >= ba.item_start[i + 1]) ++i;
+        const FwdArgs a = ba.args[i];
+        long long loc = item - ba.item_start[i];
+        const int dtile = int(loc % a.n_dtiles);
+        loc /= a.n_dtiles;
+        const int ttile = int(loc % a.n_ttiles);
+        const int b = int(loc / a.n_ttiles);
+        fwd_tile<T, DPT, SPT>(a, dtile, ttile, b, full, smem + 128, kbase);
+    }
+}
+
+namespace {
+
+struct PersistentFn {
+    const void *fn = nullptr;
+    int (*occupancy)(int block, size_t smem) = nullptr;
+};
+
+template <typename T, int DPT, int SPT>
+int occupancy_t(int block, size_t smem) {
+    if (smem > 48 * 1024 &&
+        cudaFuncSetAttribute(dd_fwd_persistent_kernel<T, DPT, SPT>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)) != cudaSuccess)
+        return 0;
+    int n = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, dd_fwd_persistent_kernel<T, DPT, SPT>,
+                                                      block, smem) != cudaSuccess)
+        return 0;
+    return n;
+}
+
+template <typename T>
+PersistentFn pick_persistent_t(int dpt, int spt) {
+#define DD_PICK(D_, S_)                                                          \
+    if (dpt == D_ && spt == S_)                                                  \
+        return PersistentFn{(const void *)&dd_fwd_persistent_kernel<T, D_, S_>, \
+                            &occupancy_t<T, D_, S_>};
+    DD_FWD_KEYS(DD_PICK)
+#undef DD_PICK
+    return PersistentFn{};
+}
+
+PersistentFn pick_persistent(dd_dtype t, int dpt, int spt) {
+    switch (t) {
+        case DD_F32: return pick_persistent_t<float>(dpt, spt);
+        case DD_F16: return pick_persistent_t<__half>(dpt, spt);
+        case DD_BF16: return pick_persistent_t<__nv_bfloat16>(dpt, spt);
+        case DD_U8: return pick_persistent_t<uint8_t>(dpt, spt);
+    }
+    return PersistentFn{};
+}
+
+}  // namespace
+}  // namespace dd
+
+struct dd_batch_s {
+    std::vector<dd_plan> plans;   // in work-list order (heaviest tile first)
+    std::vector<int> user_index;  // position of plans[i] in the caller's arrays
+    dd_dtype dtype = DD_F32;
+    dd_variant v{};
+    std::vector<dd::FwdTables> tabs;
+    std::vector<dd::FwdArgs> h_args;
+    dd::FwdArgs *d_args = nullptr;
+    unsigned long long *d_counter = nullptr;
+    dd::BatchArgs ba{};
+    size_t smem = 0;
+    int grid = 0, block = 0;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    bool args_on_device = false;
+};
+
+namespace dd {
+namespace {
+
+void release_tables(dd_batch_s *bt) {
+    for (auto &t : bt->tabs) free_fwd_tables(&t);
+    bt->tabs.clear();
+    if (bt->exec) cudaGraphExecDestroy(bt->exec);
+    if (bt->graph) cudaGraphDestroy(bt->graph);
+    bt->exec = nullptr;
+    bt->graph = nullptr;
+}
+
+// Builds tables, launch shape and graph for variant v (all plans must fit).
+dd_status configure(dd_batch_s *bt, const dd_variant &v) {
+    PersistentFn pf = pick_persistent(bt->dtype, v.dm_per_thread, v.samples_per_thread);
+    if (!pf.fn) return fail(DD_ERR_ARG, "variant not compiled");
+    std::vector<FwdTables> tabs;
+    size_t smem = 0;
+    for (dd_plan p : bt->plans) {
+        FwdTables t;
+        dd_status s = build_fwd_tables(p, v, &t);
+        if (s != DD_OK) {
+            for (auto &x : tabs) free_fwd_tables(&x);
+            return s;
+        }
+        smem = std::max(smem, t.smem_bytes);
+        tabs.push_back(t);
+    }
+    const int block = 32 * v.warps_dm * v.warps_time;
+    const int occ = pf.occupancy(block, smem);
+    if (occ < 1) {
+        for (auto &x : tabs) free_fwd_tables(&x);
+        return fail(DD_ERR_ARG, "variant does not fit one CTA per SM");
+    }
+    release_tables(bt);
+    bt->tabs = tabs;
+    bt->v = v;
+    bt->smem = smem;
+    bt->block = block;
+    bt->grid = occ * bt->plans.front()->sm_count;
+
+    const int n = int(bt->plans.size());
+    bt->h_args.assign(size_t(n), FwdArgs{});
+    bt->ba = BatchArgs{};
+    bt->ba.args = bt->d_args;
+    bt->ba.n = n;
+    bt->ba.stages = v.stages;
+    bt->ba.counter = bt->d_counter;
+    long long acc = 0;
+    for (int i = 0; i < n; ++i) {
+        dd_plan p = bt->plans[size_t(i)];
+        const FwdTables &t = bt->tabs[size_t(i)];
+        FwdArgs &a = bt->h_args[size_t(i)];
+        a.C = p->C;
+        a.D = p->D;
+        a.S = p->S;
+        a.stride = p->stride;
+        a.Dt = t.Dt;
+        a.Ts = t.Ts;
+        a.C_pad = t.C_pad;
+        a.cch = v.chans_per_stage;
+        a.stages = v.stages;
+        a.warps_dm = v.warps_dm;
+        a.stage_data_bytes = t.stage_data_bytes;
+        a.stage_offs_bytes = t.stage_offs_bytes;
+        a.n_dtiles = t.n_dtiles;
+        a.n_ttiles = t.n_ttiles;
+        a.B = p->B;
+        a.desc = t.d_desc;
+        a.offs = t.d_offs;
+        a.err = p->d_err;
+        bt->ba.item_start[i] = acc;
+        acc += (long long)t.n_dtiles * t.n_ttiles * p->B;
+    }
+    bt->ba.item_start[n] = acc;
+    bt->args_on_device = false;
+
+    // graph: counter reset -> persistent kernel
+    cudaError_t e = cudaGraphCreate(&bt->graph, 0);
+    cudaGraphNode_t mset = nullptr, kern = nullptr;
+    if (e == cudaSuccess) {
+        cudaMemsetParams mp{};
+        mp.dst = bt->d_counter;
+        mp.value = 0;
+        mp.elementSize = 4;
+        mp.width = 2;
+        mp.height = 1;
+        mp.pitch = 0;
+        e = cudaGraphAddMemsetNode(&mset, bt->graph, nullptr, 0, &mp);
+    }
+    if (e == cudaSuccess) {
+        void *params[] = {&bt->ba};
+        cudaKernelNodeParams kp{};
+        kp.func = const_cast<void *>(pf.fn);
+        kp.gridDim = dim3(unsigned(bt->grid));
+        kp.blockDim = dim3(unsigned(block));
+        kp.sharedMemBytes = unsigned(smem);
+        kp.kernelParams = params;
+        e = cudaGraphAddKernelNode(&kern, bt->graph, &mset, 1, &kp);
+    }
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&bt->exec, bt->graph, 0);
+    if (e != cudaSuccess) return cuda_fail(e, "batch graph");
+    return DD_OK;
+}
+
+double tile_cost(dd_plan p) {
+    const FwdTables &t = p->fwd;
+    return double(p->C) * t.Dt * t.Ts;
+}
+
+}  // namespace
+}  // namespace dd
+
+using namespace dd;
+
+extern "C" {
+
+dd_status dd_batch_create(dd_batch *out, int32_t n, const dd_plan *plans) {
+    if (!out) return fail(DD_ERR_ARG, "out is NULL");
+    *out = nullptr;
+    if (n < 1 || n > kMaxBatchPlans || !plans)
+        return fail(DD_ERR_ARG, "a batch holds 1..16 plans");
+    for (int i = 0; i < n; ++i) {
+        if (!plans[i]) return fail(DD_ERR_ARG, "null plan");
+        if (plans[i]->dtype != plans[0]->dtype)
+            return fail(DD_ERR_ARG, "the plans of a batch must share the input type");
+    }
+    auto *bt = new (std::nothrow) dd_batch_s;
+    if (!bt) return fail(DD_ERR_NOMEM, "host allocation");
+    std::vector<int> idx(static_cast<size_t>(n), 0);
+    for (int i = 0; i < n; ++i) idx[size_t(i)] = i;
+    std::stable_sort(idx.begin(), idx.end(),
+                     [&](int x, int y) { return tile_cost(plans[x]) > tile_cost(plans[y]); });
+    for (int i : idx) {
+        bt->plans.push_back(plans[i]);
+        bt->user_index.push_back(i);
+    }
+    bt->dtype = plans[0]->dtype;
+    cudaError_t e = cudaMalloc(&bt->d_args, sizeof(FwdArgs) * size_t(n));
+    if (e == cudaSuccess) e = cudaMalloc(&bt->d_counter, sizeof(unsigned long long));
+    if (e != cudaSuccess) {
+        dd_batch_destroy(bt);
+        return cuda_fail(e, "cudaMalloc(batch)");
+    }
+    // first plan's current variant if every plan fits it, else the defaults
+    dd_status s = configure(bt, plans[0]->fwd.v);
+    if (s != DD_OK) {
+        const int nv = dd_variant_count();
+        for (int i = 0; i < nv && s != DD_OK; ++i) {
+            dd_variant v;
+            dd_variant_get(i, &v);
+            if (v.dm_per_thread == 4 && v.samples_per_thread == 4) s = configure(bt, v);
+        }
+        for (int i = 0; i < nv && s != DD_OK; ++i) {
+            dd_variant v;
+            dd_variant_get(i, &v);
+            s = configure(bt, v);
+        }
+    }
+    if (s != DD_OK) {
+        dd_batch_destroy(bt);
+        return fail(DD_ERR_UNSUPPORTED, "no common variant fits every plan of the batch");
+    }
+    *out = bt;
+    return DD_OK;
+}
+
+dd_status dd_batch_execute(dd_batch bt, const void *const *d_in, const void *const *d_w,
+                           void *const *d_out, void *stream) {
+    if (!bt || !d_in || !d_w || !d_out) return fail(DD_ERR_ARG, "null argument");
+    bool changed = !bt->args_on_device;
+    for (size_t i = 0; i < bt->plans.size(); ++i) {
+        const int u = bt->user_index[i];
+        if (!d_in[u] || !d_w[u] || !d_out[u]) return fail(DD_ERR_ARG, "null buffer");
+        if (!aligned16(d_in[u]) || !aligned16(d_w[u]) || !aligned16(d_out[u]))
+            return fail(DD_ERR_ARG, "device pointers must be 16-byte aligned");
+        FwdArgs &a = bt->h_args[i];
+        if (a.in != d_in[u] || a.w != d_w[u] || a.out != d_out[u]) changed = true;
+        a.in = d_in[u];
+        a.w = d_w[u];
+        a.out = d_out[u];
+    }
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    cudaError_t e = cudaSuccess;
+    if (changed) {
+        e = cudaMemcpyAsync(bt->d_args, bt->h_args.data(), sizeof(FwdArgs) * bt->h_args.size(),
+                            cudaMemcpyHostToDevice, st);
+        if (e != cudaSuccess) return cuda_fail(e, "batch args upload");
+        bt->args_on_device = true;
+    }
+    e = cudaGraphLaunch(bt->exec, st);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGraphLaunch(batch)");
+    return DD_OK;
+}
+
+dd_status dd_batch_get_variant(dd_batch bt, dd_variant *v) {
+    if (!bt || !v) return fail(DD_ERR_ARG, "null argument");
+    *v = bt->v;
+    return DD_OK;
+}
+
+dd_status dd_batch_set_variant(dd_batch bt, const dd_variant *v) {
+    if (!bt || !v) return fail(DD_ERR_ARG, "null argument");
+    dd_status s = check_variant_shape(*v);
+    if (s != DD_OK) return s;
+    cudaError_t e = cudaDeviceSynchronize();
+    if (e != cudaSuccess) return cuda_fail(e, "cudaDeviceSynchronize");
+    return configure(bt, *v);
+}
+
+dd_status dd_batch_tune(dd_batch bt, int32_t budget_ms, dd_tune_report *rep) {
+    if (!bt) return fail(DD_ERR_ARG, "null batch");
+    const size_t n = bt->plans.size();
+    std::vector<void *> ins(n, nullptr), ws(n, nullptr), outs(n, nullptr);
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    cudaStream_t st = nullptr;
+    double flop = 0.0;
+    cudaError_t e = cudaSuccess;
+    for (size_t i = 0; i < n && e == cudaSuccess; ++i) {
+        dd_plan p = bt->plans[i];
+        const size_t ib = size_t(p->B) * p->C * p->stride * elt_bytes(p->dtype);
+        e = cudaMalloc(&ins[i], ib);
+        if (e == cudaSuccess) e = cudaMemset(ins[i], 0, ib);
+        if (e == cudaSuccess) e = cudaMalloc(&ws[i], size_t(p->C) * 4);
+        if (e == cudaSuccess) e = cudaMemset(ws[i], 0, size_t(p->C) * 4);
+        if (e == cudaSuccess) e = cudaMalloc(&outs[i], size_t(p->B) * p->D * p->S * 4);
+        flop += double(p->B) * p->D * double(p->S) * p->C;
+    }
+    if (e == cudaSuccess) e = cudaEventCreate(&e0);
+    if (e == cudaSuccess) e = cudaEventCreate(&e1);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking);
+    auto cleanup = [&]() {
+        for (size_t i = 0; i < n; ++i) {
+            if (ins[i]) cudaFree(ins[i]);
+            if (ws[i]) cudaFree(ws[i]);
+            if (outs[i]) cudaFree(outs[i]);
+        }
+        if (e0) cudaEventDestroy(e0);
+        if (e1) cudaEventDestroy(e1);
+        if (st) cudaStreamDestroy(st);
+        bt->args_on_device = false;
+    };
+    if (e != cudaSuccess) {
+        cleanup();
+        return cuda_fail(e, "batch tuner setup");
+    }
+    // arrays in the caller's order
+    std::vector<const void *> uin(n), uw(n);
+    std::vector<void *> uout(n);
+    for (size_t i = 0; i < n; ++i) {
+        const int u = bt->user_index[i];
+        uin[size_t(u)] = ins[i];
+        uw[size_t(u)] = ws[i];
+        uout[size_t(u)] = outs[i];
+    }
+    const dd_variant start = bt->v;
+    const auto wall0 = std::chrono::steady_clock::now();
+    std::vector<double> gflops;
+    dd_variant best = start;
+    double best_ms = 1e300;
+    const int nv = dd_variant_count();
+    for (int i = 0; i < nv; ++i) {
+        if (budget_ms > 0 && !gflops.empty() &&
+            std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - wall0)
+                    .count() > budget_ms)
+            break;
+        dd_variant v;
+        dd_variant_get(i, &v);
+        if (configure(bt, v) != DD_OK) continue;
+        bt->args_on_device = false;
+        dd_status s = dd_batch_execute(bt, uin.data(), uw.data(), uout.data(), st);
+        const int reps = 3;
+        if (s == DD_OK) e = cudaEventRecord(e0, st);
+        for (int r = 0; r < reps && s == DD_OK; ++r)
+            s = dd_batch_execute(bt, uin.data(), uw.data(), uout.data(), st);
+        if (s == DD_OK && e == cudaSuccess) e = cudaEventRecord(e1, st);
+        if (s == DD_OK && e == cudaSuccess) e = cudaEventSynchronize(e1);
+        float ms = 0.f;
+        if (s == DD_OK && e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+        if (s != DD_OK || e != cudaSuccess) {
+            cleanup();
+            return s != DD_OK ? s : cuda_fail(e, "batch tuner timing");
+        }
+        const double per = double(ms) / reps;
+        gflops.push_back(flop / (per * 1e6));
+        if (per < best_ms) {
+            best_ms = per;
+            best = v;
+        }
+    }
+    cleanup();
+    dd_status s = configure(bt, best);
+    if (s != DD_OK) return s;
+    if (gflops.empty()) return fail(DD_ERR_NOT_TUNED, "no variant fits the batch");
+    if (rep) {
+        double mean = 0.0, var = 0.0;
+        for (double g : gflops) mean += g;
+        mean /= double(gflops.size());
+        for (double g : gflops) var += (g - mean) * (g - mean);
+        const double sd = gflops.size() > 1 ? std::sqrt(var / double(gflops.size() - 1)) : 0.0;
+        rep->n_tried = int32_t(gflops.size());
+        rep->best = best;
+        rep->best_ms = best_ms;
+        rep->best_gflops = flop / (best_ms * 1e6);
+        rep->mean_gflops = mean;
+        rep->std_gflops = sd;
+        rep->snr = sd > 0 ? (rep->best_gflops - mean) / sd : 0.0;
+        rep->chebyshev = rep->snr > 1.0 ? 1.0 / (rep->snr * rep->snr) : 1.0;
+    }
+    return DD_OK;
+}
+
+void dd_batch_destroy(dd_batch bt) {
+    if (!bt) return;
+    release_tables(bt);
+    if (bt->d_args) cudaFree(bt->d_args);
+    if (bt->d_counter) cudaFree(bt->d_counter);
+    delete bt;
+}
+
+}  // extern "C"

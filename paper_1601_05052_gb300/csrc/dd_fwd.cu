@@ -1,0 +1,148 @@
+// dd_fwd.cu -- forward dedispersion kernel for sm_103a and its launcher.
+//
+// Computes out[b][d][t] = sum_c w[c] * in[b][c][t + shift[d][c]] (Algorithm
+// 1, Section III-A, with weights) with one CTA per (DM tile, time tile,
+// beam); the tile body is in dd_fwd_tile.cuh. Grid x runs over DM tiles so
+// that CTAs resident at the same time share time ranges and the input
+// windows they stage stay in L2.
+#include <atomic>
+
+#include "dd_fwd_tile.cuh"
+#include "dd_internal.h"
+
+namespace dd {
+
+template <typename T, int DPT, int SPT>
+__global__ void __launch_bounds__(256, 1) dd_fwd_kernel(const FwdArgs a) {
+    extern __shared__ __align__(128) unsigned char smem[];
+    uint64_t *full = reinterpret_cast<uint64_t *>(smem);
+    fwd_init_barriers(full, a.stages);
+    uint32_t kbase = 0;
+    fwd_tile<T, DPT, SPT>(a, blockIdx.x, blockIdx.y, blockIdx.z, full, smem + 128, kbase);
+}
+
+namespace {
+
+using FwdLaunchFn = cudaError_t (*)(const FwdArgs &, dim3, dim3, size_t, cudaStream_t);
+
+template <typename T, int DPT, int SPT>
+cudaError_t launch_fwd_t(const FwdArgs &a, dim3 grid, dim3 block, size_t smem, cudaStream_t st) {
+    // Raise the kernel's dynamic shared-memory limit once per size increase.
+    static std::atomic<size_t> smem_set{0};
+    if (smem > 48 * 1024 && smem > smem_set.load()) {
+        cudaError_t e = cudaFuncSetAttribute(dd_fwd_kernel<T, DPT, SPT>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             int(smem));
+        if (e != cudaSuccess) return e;
+        smem_set.store(smem);
+    }
+    dd_fwd_kernel<T, DPT, SPT><<<grid, block, smem, st>>>(a);
+    return cudaGetLastError();
+}
+
+template <typename T>
+FwdLaunchFn pick(int dpt, int spt) {
+#define DD_PICK(D_, S_) \
+    if (dpt == D_ && spt == S_) return &launch_fwd_t<T, D_, S_>;
+    DD_FWD_KEYS(DD_PICK)
+#undef DD_PICK
+    return nullptr;
+}
+
+FwdLaunchFn pick_fn(dd_dtype t, int dpt, int spt) {
+    switch (t) {
+        case DD_F32: return pick<float>(dpt, spt);
+        case DD_F16: return pick<__half>(dpt, spt);
+        case DD_BF16: return pick<__nv_bfloat16>(dpt, spt);
+        case DD_U8: return pick<uint8_t>(dpt, spt);
+    }
+    return nullptr;
+}
+
+}  // namespace
+
+const std::vector<FwdKernelKey> &fwd_compiled_keys() {
+    static const std::vector<FwdKernelKey> keys = {
+#define DD_KEY(D_, S_) FwdKernelKey{D_, S_},
+        DD_FWD_KEYS(DD_KEY)
+#undef DD_KEY
+    };
+    return keys;
+}
+
+bool fwd_variant_compiled(int dpt, int spt) { return pick_fn(DD_F32, dpt, spt) != nullptr; }
+
+dd_status launch_forward(dd_plan_s *p, const FwdTables &t, const void *in, const void *w,
+                         void *out, cudaStream_t st) {
+    FwdLaunchFn fn = pick_fn(p->dtype, t.v.dm_per_thread, t.v.samples_per_thread);
+    if (!fn) return fail(DD_ERR_UNSUPPORTED, "forward variant not compiled");
+    FwdArgs a;
+    a.in = in;
+    a.w = w;
+    a.out = out;
+    a.C = p->C;
+    a.D = p->D;
+    a.S = p->S;
+    a.stride = p->stride;
+    a.Dt = t.Dt;
+    a.Ts = t.Ts;
+    a.C_pad = t.C_pad;
+    a.cch = t.v.chans_per_stage;
+    a.stages = t.v.stages;
+    a.warps_dm = t.v.warps_dm;
+    a.stage_data_bytes = t.stage_data_bytes;
+    a.stage_offs_bytes = t.stage_offs_bytes;
+    a.n_dtiles = t.n_dtiles;
+    a.n_ttiles = t.n_ttiles;
+    a.B = p->B;
+    a.desc = t.d_desc;
+    a.offs = t.d_offs;
+    a.err = p->d_err;
+    dim3 grid(unsigned(t.n_dtiles), unsigned(t.n_ttiles), unsigned(p->B));
+    dim3 block(unsigned(32 * t.v.warps_dm * t.v.warps_time));
+    cudaError_t e = fn(a, grid, block, t.smem_bytes, st);
+    if (e != cudaSuccess) return cuda_fail(e, "forward launch");
+    return DD_OK;
+}
+
+}  // namespace dd
+
+using namespace dd;
+
+extern "C" {
+
+dd_status dd_execute(dd_plan p, const void *d_in, const void *d_w, void *d_out, void *stream) {
+    if (!p || !d_in || !d_w || !d_out) return fail(DD_ERR_ARG, "null argument");
+    if (!aligned16(d_in) || !aligned16(d_w) || !aligned16(d_out))
+        return fail(DD_ERR_ARG, "device pointers must be 16-byte aligned");
+    return launch_forward(p, p->fwd, d_in, d_w, d_out, static_cast<cudaStream_t>(stream));
+}
+
+dd_status dd_execute_host(dd_plan p, const void *h_in, const void *h_w, void *h_out,
+                          void *stream) {
+    if (!p || !h_in || !h_w || !h_out) return fail(DD_ERR_ARG, "null argument");
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    const size_t in_bytes = size_t(p->B) * p->C * p->stride * elt_bytes(p->dtype);
+    const size_t w_bytes = size_t(p->C) * 4;
+    const size_t out_bytes = size_t(p->B) * p->D * p->S * 4;
+    {
+        std::lock_guard<std::mutex> lk(p->mu);
+        cudaError_t e = cudaSuccess;
+        if (!p->h_in_dev) e = cudaMalloc(&p->h_in_dev, in_bytes);
+        if (e == cudaSuccess && !p->h_w_dev) e = cudaMalloc(&p->h_w_dev, w_bytes);
+        if (e == cudaSuccess && !p->h_out_dev) e = cudaMalloc(&p->h_out_dev, out_bytes);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaMalloc(host mirrors)");
+    }
+    cudaError_t e = cudaMemcpyAsync(p->h_in_dev, h_in, in_bytes, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(p->h_w_dev, h_w, w_bytes, cudaMemcpyHostToDevice, st);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaMemcpyAsync(H2D)");
+    dd_status s = launch_forward(p, p->fwd, p->h_in_dev, p->h_w_dev, p->h_out_dev, st);
+    if (s != DD_OK) return s;
+    e = cudaMemcpyAsync(h_out, p->h_out_dev, out_bytes, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaMemcpyAsync(D2H)/sync");
+    return DD_OK;
+}
+
+}  // extern "C"

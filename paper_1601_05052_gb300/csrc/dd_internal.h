@@ -1,0 +1,119 @@
+// dd_internal.h -- plan state and kernel-launch interfaces shared by the
+// translation units of libdd.so. Not part of the public ABI (see dd.h).
+#pragma once
+#include <cuda_runtime.h>
+
+#include <cstddef>
+#include <cstdint>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "../../include/dd.h"
+#include "dd_errbits.h"
+
+namespace dd {
+
+inline int elt_bytes(dd_dtype t) { return t == DD_F32 ? 4 : (t == DD_U8 ? 1 : 2); }
+// Elements per 16 bytes: the TMA bulk-copy granule.
+inline int align_elems(dd_dtype t) { return 16 / elt_bytes(t); }
+
+// Per-variant staging tables of the forward kernel.
+//
+// The DM axis is cut into tiles of Dt trials, the time axis into tiles of Ts
+// output samples. For DM tile k and channel c, every trial of the tile reads
+// input samples [t0 + smin, t0 + smax + Ts) of row c, where smin/smax are
+// the tile's smallest/largest delay in that channel (Section III-B: a 2-D
+// work-group shares the union of its trials' inputs). That window, widened
+// to 16-byte granules, is copied into shared memory once per stage.
+//
+//   desc[k][c] = {win_start (elements, relative to t0, 16-byte aligned),
+//                 win_len (elements, multiple of 16 bytes),
+//                 smem_off (element offset of the window in the stage buffer),
+//                 0}
+//   offs[k][c][i] = smem element offset of sample t0 of trial k*Dt + i
+//                   in channel c (= smem_off + shift - win_start)
+struct FwdTables {
+    dd_variant v{};
+    int Dt = 0, Ts = 0;
+    int n_dtiles = 0, n_ttiles = 0;
+    int C_pad = 0;               // channels rounded up to chans_per_stage
+    int stage_elems = 0;         // data elements in one stage buffer
+    int stage_data_bytes = 0;    // rounded to 16
+    int stage_offs_bytes = 0;    // chans_per_stage * Dt * 2, rounded to 16
+    size_t smem_bytes = 0;       // dynamic shared memory of one CTA
+    int4 *d_desc = nullptr;
+    uint16_t *d_offs = nullptr;
+};
+
+// Tables of the adjoint (gather) kernel: the roles of channels and trials
+// swap. A CTA owns a tile of Ct channels by Tt input samples and stages, per
+// trial d, the cotangent samples g[d][tau0 - A_d, tau0 - A_d + len_d) with
+// A_d = smax_d rounded up to 4 (smax_d/smin_d over the channel tile).
+//   adesc[k][d] = {A_d, len_d, smem_off, 0}
+//   aoffs[k][d][j] = smem_off + A_d - shift[d][k*Ct + j]
+struct AdjTables {
+    int Ct = 0, Tt = 0, cpt = 0, spt = 0, wc = 0, wt = 0, dch = 0;
+    int n_ctiles = 0, n_ttiles = 0, D_pad = 0;
+    int stage_elems = 0;
+    size_t smem_bytes = 0;
+    int4 *d_desc = nullptr;
+    uint16_t *d_offs = nullptr;
+    float *d_part = nullptr;     // [n_ttiles][B][C] grad_w partial sums (scratch)
+};
+
+}  // namespace dd
+
+struct dd_plan_s {
+    int32_t C = 0, D = 0, B = 0;
+    int64_t S = 0, T_in = 0, stride = 0;
+    dd_dtype dtype = DD_F32;
+    int32_t max_shift = 0;
+    std::vector<int32_t> shifts;  // [D][C]
+
+    int device = 0;
+    int sm_count = 0;
+    size_t smem_optin = 0;
+
+    dd::FwdTables fwd;
+    dd::AdjTables adj;
+    int *d_err = nullptr;         // device error word (dd::kErr* bits)
+
+    // device mirrors for dd_execute_host, allocated on first use
+    void *h_in_dev = nullptr, *h_w_dev = nullptr, *h_out_dev = nullptr;
+
+    std::mutex mu;
+};
+
+namespace dd {
+
+// Thread-local error reporting (implemented in dd_plan.cpp).
+dd_status fail(dd_status s, const std::string &msg);
+dd_status cuda_fail(cudaError_t e, const char *what);
+dd_status ok();
+
+// Compiled forward variants: (dm_per_thread, samples_per_thread) pairs with
+// a kernel for every input type.
+struct FwdKernelKey { int dpt, spt; };
+const std::vector<FwdKernelKey> &fwd_compiled_keys();
+bool fwd_variant_compiled(int dpt, int spt);
+
+// Builds (or rebuilds) the forward tables for variant v; DD_ERR_ARG if v does
+// not fit this plan/device.
+dd_status build_fwd_tables(dd_plan_s *p, const dd_variant &v, FwdTables *out);
+void free_fwd_tables(FwdTables *t);
+dd_status check_variant_shape(const dd_variant &v);
+
+// Enqueue the forward kernel with the plan's current tables.
+dd_status launch_forward(dd_plan_s *p, const FwdTables &t, const void *in, const void *w,
+                         void *out, cudaStream_t st);
+
+// Adjoint
+dd_status ensure_adj_tables(dd_plan_s *p);
+void free_adj_tables(AdjTables *t);
+dd_status launch_adjoint(dd_plan_s *p, const float *g, const float *w, const float *in,
+                         float *gin, float *gw, cudaStream_t st);
+
+bool aligned16(const void *p);
+
+}  // namespace dd

@@ -1,0 +1,351 @@
+// dd_plan.cpp -- host side of libdd: the Eq. 1 delay table, plan creation,
+// the per-variant staging tables of the forward kernel, the variant grid and
+// the thread-local error state of the C ABI.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <limits>
+
+#include "dd_internal.h"
+
+namespace dd {
+
+namespace {
+thread_local dd_status tl_status = DD_OK;
+thread_local std::string tl_msg;
+
+// Dispersion constant of Eq. 1 in MHz^2 pc^-1 cm^3 s (the paper prints the
+// rounded value 4150).
+constexpr double kDispersionConst = 4.148808e3;
+constexpr int64_t kMaxShift = int64_t(1) << 30;
+
+int64_t round_up(int64_t x, int64_t m) { return (x + m - 1) / m * m; }
+int64_t floor_to(int64_t x, int64_t m) { return x >= 0 ? x / m * m : -((-x + m - 1) / m) * m; }
+}  // namespace
+
+dd_status fail(dd_status s, const std::string &msg) {
+    tl_status = s;
+    tl_msg = msg;
+    return s;
+}
+dd_status cuda_fail(cudaError_t e, const char *what) {
+    return fail(e == cudaErrorMemoryAllocation ? DD_ERR_NOMEM : DD_ERR_CUDA,
+                std::string(what) + ": " + cudaGetErrorString(e));
+}
+dd_status ok() { return DD_OK; }
+
+bool aligned16(const void *p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
+
+dd_status check_variant_shape(const dd_variant &v) {
+    if (!fwd_variant_compiled(v.dm_per_thread, v.samples_per_thread))
+        return fail(DD_ERR_ARG, "variant (dm_per_thread, samples_per_thread) not compiled");
+    if (v.warps_dm < 1 || v.warps_time < 1 || v.warps_dm * v.warps_time > 8)
+        return fail(DD_ERR_ARG, "variant warps_dm * warps_time must be in [1, 8]");
+    if (v.chans_per_stage != 4 && v.chans_per_stage != 8 && v.chans_per_stage != 16)
+        return fail(DD_ERR_ARG, "variant chans_per_stage must be 4, 8 or 16");
+    if (v.stages < 2 || v.stages > 4) return fail(DD_ERR_ARG, "variant stages must be 2..4");
+    return DD_OK;
+}
+
+dd_status build_fwd_tables(dd_plan_s *p, const dd_variant &v, FwdTables *out) {
+    dd_status s = check_variant_shape(v);
+    if (s != DD_OK) return s;
+    FwdTables t;
+    t.v = v;
+    t.Dt = v.dm_per_thread * v.warps_dm;
+    t.Ts = 32 * v.samples_per_thread * v.warps_time;
+    t.n_dtiles = (p->D + t.Dt - 1) / t.Dt;
+    t.n_ttiles = static_cast<int>((p->S + t.Ts - 1) / t.Ts);
+    const int cch = v.chans_per_stage;
+    t.C_pad = (p->C + cch - 1) / cch * cch;
+    const int al = align_elems(p->dtype);
+    const int elt = elt_bytes(p->dtype);
+    if (t.n_ttiles > 65535) return fail(DD_ERR_ARG, "too many time tiles for this variant");
+
+    std::vector<int4> desc(size_t(t.n_dtiles) * t.C_pad, make_int4(0, 0, 0, 0));
+    std::vector<uint16_t> offs(size_t(t.n_dtiles) * t.C_pad * t.Dt, 0);
+    int64_t stage_max = 0;
+    for (int k = 0; k < t.n_dtiles; ++k) {
+        const int d0 = k * t.Dt, d1 = std::min(p->D, d0 + t.Dt);
+        for (int c0 = 0; c0 < p->C; c0 += cch) {
+            int64_t soff = 0;
+            for (int c = c0; c < std::min(p->C, c0 + cch); ++c) {
+                int32_t smin = std::numeric_limits<int32_t>::max(), smax = 0;
+                for (int d = d0; d < d1; ++d) {
+                    const int32_t sh = p->shifts[size_t(d) * p->C + c];
+                    smin = std::min(smin, sh);
+                    smax = std::max(smax, sh);
+                }
+                const int64_t ws = floor_to(smin, al);
+                const int64_t len = round_up(smax + t.Ts - ws, al);
+                if (soff + len > 65536) return fail(DD_ERR_ARG, "stage too large for variant");
+                desc[size_t(k) * t.C_pad + c] =
+                    make_int4(int(ws), int(len), int(soff), 0);
+                for (int i = 0; i < t.Dt; ++i) {
+                    const int d = d0 + i;
+                    const int64_t o = d < p->D ? soff + p->shifts[size_t(d) * p->C + c] - ws : soff;
+                    offs[(size_t(k) * t.C_pad + c) * t.Dt + i] = static_cast<uint16_t>(o);
+                }
+                soff += len;
+            }
+            stage_max = std::max(stage_max, soff);
+        }
+    }
+    t.stage_elems = static_cast<int>(stage_max);
+    t.stage_data_bytes = static_cast<int>(round_up(stage_max * elt, 16));
+    t.stage_offs_bytes = static_cast<int>(round_up(int64_t(cch) * t.Dt * 2, 16));
+    t.smem_bytes = 128 + size_t(v.stages) * (t.stage_data_bytes + t.stage_offs_bytes);
+    if (t.smem_bytes > p->smem_optin)
+        return fail(DD_ERR_ARG, "variant needs more shared memory than the device has");
+
+    cudaError_t e = cudaMalloc(&t.d_desc, desc.size() * sizeof(int4));
+    if (e != cudaSuccess) return cuda_fail(e, "cudaMalloc(desc)");
+    e = cudaMalloc(&t.d_offs, offs.size() * sizeof(uint16_t));
+    if (e != cudaSuccess) {
+        cudaFree(t.d_desc);
+        return cuda_fail(e, "cudaMalloc(offs)");
+    }
+    e = cudaMemcpy(t.d_desc, desc.data(), desc.size() * sizeof(int4), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess)
+        e = cudaMemcpy(t.d_offs, offs.data(), offs.size() * sizeof(uint16_t),
+                       cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) {
+        free_fwd_tables(&t);
+        return cuda_fail(e, "cudaMemcpy(tables)");
+    }
+    *out = t;
+    return DD_OK;
+}
+
+void free_fwd_tables(FwdTables *t) {
+    if (t->d_desc) cudaFree(t->d_desc);
+    if (t->d_offs) cudaFree(t->d_offs);
+    t->d_desc = nullptr;
+    t->d_offs = nullptr;
+}
+
+namespace {
+
+// Candidate default variants, best first; the first that fits the plan is
+// used until dd_tune or dd_plan_set_variant picks another.
+const dd_variant kDefaults[] = {
+    {4, 4, 4, 2, 8, 3}, {4, 4, 4, 2, 4, 2}, {2, 4, 4, 2, 4, 2}, {2, 2, 4, 2, 4, 2},
+};
+
+dd_status finish_plan(dd_plan_s *p, dd_plan *out) {
+    p->max_shift = 0;
+    for (int32_t s : p->shifts) p->max_shift = std::max(p->max_shift, s);
+    p->T_in = p->S + p->max_shift;
+    p->stride = round_up(p->T_in, align_elems(p->dtype));
+
+    cudaError_t e = cudaGetDevice(&p->device);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
+    int v = 0;
+    e = cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, p->device);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaDeviceGetAttribute(SMs)");
+    p->sm_count = v;
+    e = cudaDeviceGetAttribute(&v, cudaDevAttrMaxSharedMemoryPerBlockOptin, p->device);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaDeviceGetAttribute(smem)");
+    p->smem_optin = size_t(v);
+    e = cudaMalloc(&p->d_err, sizeof(int));
+    if (e != cudaSuccess) return cuda_fail(e, "cudaMalloc(err)");
+    e = cudaMemset(p->d_err, 0, sizeof(int));
+    if (e != cudaSuccess) return cuda_fail(e, "cudaMemset(err)");
+
+    dd_status s = DD_ERR_UNSUPPORTED;
+    for (const dd_variant &dv : kDefaults) {
+        s = build_fwd_tables(p, dv, &p->fwd);
+        if (s == DD_OK) break;
+        if (s != DD_ERR_ARG) return s;
+    }
+    if (s != DD_OK)
+        return fail(DD_ERR_UNSUPPORTED, "no forward variant fits this plan (delay spans too wide)");
+    *out = p;
+    return ok();
+}
+
+dd_status check_common(dd_plan *out, int32_t n_chan, int32_t n_dm, int64_t n_out,
+                       int32_t batch, dd_dtype t) {
+    if (!out) return fail(DD_ERR_ARG, "out is NULL");
+    *out = nullptr;
+    if (n_chan < 1 || n_dm < 1 || n_out < 1 || batch < 1)
+        return fail(DD_ERR_ARG, "n_chan, n_dm, n_out and batch must be >= 1");
+    if (t != DD_F32 && t != DD_F16 && t != DD_BF16 && t != DD_U8)
+        return fail(DD_ERR_ARG, "unknown input dtype");
+    if (n_out > (int64_t(1) << 31) - (int64_t(1) << 30) || batch > 65535)
+        return fail(DD_ERR_ARG, "n_out or batch too large");
+    return DD_OK;
+}
+
+}  // namespace
+}  // namespace dd
+
+using namespace dd;
+
+extern "C" {
+
+dd_status dd_compute_shifts(int32_t n_chan, const double *freq_mhz, double f_ref_mhz,
+                            double t_samp_s, int32_t n_dm, const double *dm,
+                            int32_t *shifts) {
+    if (!freq_mhz || !dm || !shifts) return fail(DD_ERR_ARG, "null pointer");
+    if (n_chan < 1 || n_dm < 1) return fail(DD_ERR_ARG, "n_chan and n_dm must be >= 1");
+    if (!(t_samp_s > 0.0) || !std::isfinite(t_samp_s))
+        return fail(DD_ERR_ARG, "t_samp must be positive and finite");
+    if (!(f_ref_mhz > 0.0) || !std::isfinite(f_ref_mhz))
+        return fail(DD_ERR_ARG, "f_ref must be positive and finite");
+    for (int32_t c = 0; c < n_chan; ++c)
+        if (!(freq_mhz[c] > 0.0) || !std::isfinite(freq_mhz[c]))
+            return fail(DD_ERR_ARG, "channel frequencies must be positive and finite");
+    for (int32_t d = 0; d < n_dm; ++d)
+        if (!std::isfinite(dm[d])) return fail(DD_ERR_ARG, "DM values must be finite");
+    const double ref_term = 1.0 / (f_ref_mhz * f_ref_mhz);
+    for (int32_t d = 0; d < n_dm; ++d) {
+        const double k_dm = kDispersionConst * dm[d];
+        for (int32_t c = 0; c < n_chan; ++c) {
+            const double f = freq_mhz[c];
+            const double delay_s = k_dm * (1.0 / (f * f) - ref_term);
+            const double r = std::llround(delay_s / t_samp_s);
+            if (r < 0) return fail(DD_ERR_ARG, "negative delay: channel above f_ref or DM < 0");
+            if (r > double(kMaxShift)) return fail(DD_ERR_ARG, "delay exceeds 2^30 samples");
+            shifts[size_t(d) * n_chan + c] = static_cast<int32_t>(r);
+        }
+    }
+    return DD_OK;
+}
+
+dd_status dd_plan_create(dd_plan *out, int32_t n_chan, const double *freq_mhz,
+                         double f_ref_mhz, double t_samp_s, int32_t n_dm, const double *dm,
+                         int64_t n_out, int32_t batch, dd_dtype in_dtype) {
+    dd_status s = check_common(out, n_chan, n_dm, n_out, batch, in_dtype);
+    if (s != DD_OK) return s;
+    auto *p = new (std::nothrow) dd_plan_s;
+    if (!p) return fail(DD_ERR_NOMEM, "host allocation");
+    p->C = n_chan;
+    p->D = n_dm;
+    p->B = batch;
+    p->S = n_out;
+    p->dtype = in_dtype;
+    p->shifts.resize(size_t(n_dm) * n_chan);
+    s = dd_compute_shifts(n_chan, freq_mhz, f_ref_mhz, t_samp_s, n_dm, dm, p->shifts.data());
+    if (s == DD_OK) s = finish_plan(p, out);
+    if (s != DD_OK) dd_plan_destroy(p);
+    return s;
+}
+
+dd_status dd_plan_create_from_shifts(dd_plan *out, int32_t n_chan, int32_t n_dm,
+                                     const int32_t *shifts, int64_t n_out, int32_t batch,
+                                     dd_dtype in_dtype) {
+    dd_status s = check_common(out, n_chan, n_dm, n_out, batch, in_dtype);
+    if (s != DD_OK) return s;
+    if (!shifts) return fail(DD_ERR_ARG, "shifts is NULL");
+    for (size_t i = 0; i < size_t(n_chan) * n_dm; ++i)
+        if (shifts[i] < 0 || shifts[i] > kMaxShift)
+            return fail(DD_ERR_ARG, "shifts must lie in [0, 2^30]");
+    auto *p = new (std::nothrow) dd_plan_s;
+    if (!p) return fail(DD_ERR_NOMEM, "host allocation");
+    p->C = n_chan;
+    p->D = n_dm;
+    p->B = batch;
+    p->S = n_out;
+    p->dtype = in_dtype;
+    p->shifts.assign(shifts, shifts + size_t(n_dm) * n_chan);
+    s = finish_plan(p, out);
+    if (s != DD_OK) dd_plan_destroy(p);
+    return s;
+}
+
+void dd_plan_destroy(dd_plan p) {
+    if (!p) return;
+    free_fwd_tables(&p->fwd);
+    free_adj_tables(&p->adj);
+    if (p->d_err) cudaFree(p->d_err);
+    if (p->h_in_dev) cudaFree(p->h_in_dev);
+    if (p->h_w_dev) cudaFree(p->h_w_dev);
+    if (p->h_out_dev) cudaFree(p->h_out_dev);
+    delete p;
+}
+
+int64_t dd_plan_input_len(dd_plan p) { return p ? p->T_in : -1; }
+int64_t dd_plan_input_stride(dd_plan p) { return p ? p->stride : -1; }
+int32_t dd_plan_max_shift(dd_plan p) { return p ? p->max_shift : -1; }
+
+dd_status dd_plan_shifts(dd_plan p, int32_t *host_dst) {
+    if (!p || !host_dst) return fail(DD_ERR_ARG, "null argument");
+    std::memcpy(host_dst, p->shifts.data(), p->shifts.size() * sizeof(int32_t));
+    return DD_OK;
+}
+
+dd_status dd_plan_get_variant(dd_plan p, dd_variant *v) {
+    if (!p || !v) return fail(DD_ERR_ARG, "null argument");
+    *v = p->fwd.v;
+    return DD_OK;
+}
+
+dd_status dd_plan_set_variant(dd_plan p, const dd_variant *v) {
+    if (!p || !v) return fail(DD_ERR_ARG, "null argument");
+    std::lock_guard<std::mutex> lk(p->mu);
+    FwdTables t;
+    dd_status s = build_fwd_tables(p, *v, &t);
+    if (s != DD_OK) return s;
+    cudaError_t e = cudaDeviceSynchronize();  // no launch may still read the old tables
+    free_fwd_tables(&p->fwd);
+    p->fwd = t;
+    if (e != cudaSuccess) return cuda_fail(e, "cudaDeviceSynchronize");
+    return DD_OK;
+}
+
+int32_t dd_variant_count(void) {
+    static const int wshapes = 7, cchs = 3, stages = 3;
+    return int32_t(fwd_compiled_keys().size()) * wshapes * cchs * stages;
+}
+
+dd_status dd_variant_get(int32_t i, dd_variant *v) {
+    static const int W[7][2] = {{4, 2}, {2, 4}, {8, 1}, {1, 8}, {4, 1}, {2, 2}, {1, 4}};
+    static const int CCH[3] = {8, 4, 16};
+    if (!v || i < 0 || i >= dd_variant_count()) return fail(DD_ERR_ARG, "variant index");
+    const auto &keys = fwd_compiled_keys();
+    const int st = i % 3;
+    i /= 3;
+    const int cc = i % 3;
+    i /= 3;
+    const int ws = i % 7;
+    i /= 7;
+    const FwdKernelKey k = keys[size_t(i)];
+    *v = dd_variant{k.dpt, k.spt, W[ws][0], W[ws][1], CCH[cc], 2 + st};
+    return DD_OK;
+}
+
+dd_status dd_plan_check_device(dd_plan p) {
+    if (!p) return fail(DD_ERR_ARG, "null plan");
+    cudaError_t e = cudaDeviceSynchronize();
+    if (e != cudaSuccess) return cuda_fail(e, "cudaDeviceSynchronize");
+    int h = 0;
+    e = cudaMemcpy(&h, p->d_err, sizeof(int), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaMemcpy(err)");
+    e = cudaMemset(p->d_err, 0, sizeof(int));
+    if (e != cudaSuccess) return cuda_fail(e, "cudaMemset(err)");
+    if (h & kErrWaitTimeout) return fail(DD_ERR_TIMEOUT, "a kernel gave up a bounded wait");
+    if (h) return fail(DD_ERR_DEVICE, "a kernel reported a device-side error");
+    return DD_OK;
+}
+
+const char *dd_status_str(dd_status s) {
+    switch (s) {
+        case DD_OK: return "DD_OK";
+        case DD_ERR_ARG: return "DD_ERR_ARG";
+        case DD_ERR_CUDA: return "DD_ERR_CUDA";
+        case DD_ERR_NOMEM: return "DD_ERR_NOMEM";
+        case DD_ERR_UNSUPPORTED: return "DD_ERR_UNSUPPORTED";
+        case DD_ERR_TIMEOUT: return "DD_ERR_TIMEOUT";
+        case DD_ERR_NOT_TUNED: return "DD_ERR_NOT_TUNED";
+        case DD_ERR_DEVICE: return "DD_ERR_DEVICE";
+    }
+    return "DD_ERR_UNKNOWN";
+}
+
+dd_status dd_get_last_error(void) { return tl_status; }
+const char *dd_last_error_message(void) { return tl_msg.c_str(); }
+int32_t dd_version(void) { return DD_VERSION; }
+
+}  // extern "C"

@@ -1,0 +1,172 @@
+"""GPU parity of the forward kernel against the FP64 oracle: every input type,
+ragged shapes spanning several tiles, edge cases, the variant grid, and the
+full-size survey workload at the benchmark's launch configuration (sampled)."""
+import zlib
+
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import synth
+from paper_1601_05052_gb300 import Plan, variants
+from gpu_util import assert_float_parity, check_full, random_case, to_dev, weights_dev
+
+pytestmark = pytest.mark.gpu
+DTYPES = ["f32", "f16", "bf16", "u8"]
+
+
+def _setup_case(name, dtype, wkind, seed):
+    s = synth.setup(name).with_(dtype=dtype)
+    sh = oracle.shift_table(s.freqs(), s.f_ref, s.t_samp, s.dms())
+    pulses = synth.pulse_plan(s, seed, fixed=(40, 1000, 5.0))
+    x = synth.make_input(s, sh, seed=seed, pulses=pulses)
+    w = synth.make_weights(s.n_chan, seed, wkind)
+    if dtype == "u8":
+        w = synth.quantize_weights_q8(w)
+    return s, sh, x, w
+
+
+def test_workload1_plain_f32_full():
+    """64 channels, 64 trials, 4096 samples, FP32, unit weights, one pulse."""
+    s, sh, x, w = _setup_case("cfg1", "f32", "ones", 1)
+    plan = Plan.from_setup(s)
+    np.testing.assert_array_equal(plan.shifts(), sh)
+    out = check_full(plan, x, w, sh, "f32", "cfg1")
+    d, t = np.unravel_index(np.argmax(out[0]), out[0].shape)
+    assert t == 1000 and abs(int(d) - 40) <= 1
+    plan.check_device()
+
+
+@pytest.mark.parametrize("dtype", ["u8", "f16", "bf16"])
+def test_workload3_precision_forms_full(dtype):
+    """Workload 1's shapes and pulse with weights U(0.5,1.5), 5% masked:
+    u8 bit-exact (int32), f16/bf16 within 1e-4 * sum|w*in|."""
+    s, sh, x, w = _setup_case("cfg3_" + dtype, dtype, "uniform", 3)
+    plan = Plan.from_setup(s)
+    check_full(plan, x, w, sh, dtype, "cfg3 " + dtype)
+    plan.check_device()
+
+
+RAGGED = [  # (B, C, D, S, max_shift)
+    (3, 37, 29, 1000, 150),
+    (2, 5, 70, 333, 900),
+    (1, 130, 3, 2049, 20),
+    (1, 1, 1, 1, 0),
+    (2, 64, 33, 4097, 4000),
+]
+
+
+@pytest.mark.parametrize("dtype", DTYPES)
+@pytest.mark.parametrize("case", RAGGED)
+def test_ragged_shapes_default_variant(dtype, case):
+    rng = np.random.default_rng(zlib.crc32(repr((dtype, case)).encode()))
+    sh, x, w = random_case(rng, *case, dtype=dtype)
+    plan = Plan(shifts=sh, n_out=case[3], batch=case[0], dtype=dtype)
+    check_full(plan, x, w, sh, dtype, "ragged %s %s" % (dtype, case))
+
+
+@pytest.mark.parametrize("dtype", DTYPES)
+def test_non_monotone_tables_and_dm0(dtype):
+    rng = np.random.default_rng(5)
+    sh, x, w = random_case(rng, 2, 19, 23, 700, 300, dtype, monotone=False)
+    plan = Plan(shifts=sh, n_out=700, batch=2, dtype=dtype)
+    check_full(plan, x, w, sh, dtype, "non-monotone")
+    # Section IV-C: all trials at DM 0 -> every row is the weighted channel sum
+    sh0, x0, w0 = random_case(rng, 1, 50, 17, 900, 0, dtype)
+    plan0 = Plan(shifts=sh0, n_out=900, batch=1, dtype=dtype)
+    out = check_full(plan0, x0, w0, sh0, dtype, "dm0")
+    assert (out[0] == out[0, :1]).all()
+
+
+def _variant_subset():
+    vs = variants()
+    picked, seen = [], set()
+    for v in vs:
+        key = (v["dm_per_thread"], v["samples_per_thread"], v["warps_dm"], v["warps_time"])
+        if key in seen:
+            continue
+        seen.add(key)
+        picked.append(v)
+    # also every staging depth / chunk size once
+    for v in vs:
+        if v["dm_per_thread"] == 4 and v["samples_per_thread"] == 4 and v["warps_dm"] == 4:
+            picked.append(v)
+    return picked
+
+
+@pytest.mark.parametrize("dtype", DTYPES)
+def test_every_variant_shape(dtype):
+    rng = np.random.default_rng(77)
+    sh, x, w = random_case(rng, 2, 41, 45, 1500, 260, dtype)
+    plan = Plan(shifts=sh, n_out=1500, batch=2, dtype=dtype)
+    xd, wd = to_dev(x, dtype), weights_dev(w, dtype)
+    if dtype == "u8":
+        ref = oracle.forward_u8(x, w, sh, 1500)
+    else:
+        ref, ab = oracle.forward(x, w, sh, 1500, dtype=dtype, with_absum=True)
+    n = 0
+    for v in _variant_subset():
+        try:
+            plan.variant = v
+        except Exception:
+            continue  # does not fit this plan
+        out = plan.execute(xd, wd).cpu().numpy()
+        if dtype == "u8":
+            np.testing.assert_array_equal(out.astype(np.int64), ref, err_msg=str(v))
+        else:
+            assert_float_parity(out, ref, ab, what=str(v))
+        n += 1
+    assert n >= 10
+    plan.check_device()
+
+
+def test_execute_host_matches_device_path():
+    rng = np.random.default_rng(9)
+    sh, x, w = random_case(rng, 2, 30, 40, 800, 100, "f32")
+    plan = Plan(shifts=sh, n_out=800, batch=2)
+    dev = plan.execute(to_dev(x, "f32"), weights_dev(w, "f32")).cpu()
+    hx = torch.from_numpy(x).pin_memory()
+    hw = torch.from_numpy(w).pin_memory()
+    hout = torch.empty(plan.out_shape, dtype=torch.float32).pin_memory()
+    plan.execute_host(hx, hw, hout)
+    assert torch.equal(dev, hout)
+
+
+def test_tuned_variant_stays_correct():
+    rng = np.random.default_rng(10)
+    sh, x, w = random_case(rng, 1, 96, 64, 3000, 400, "f32")
+    plan = Plan(shifts=sh, n_out=3000, batch=1)
+    rep = plan.tune(budget_ms=3000)
+    assert rep["n_tried"] >= 2 and rep["best_gflops"] >= rep["mean_gflops"]
+    assert plan.variant == rep["best"]
+    check_full(plan, x, w, sh, "f32", "tuned")
+
+
+def test_survey_scale_f32_sampled():
+    """The benchmark workload (1024 ch, 2048 trials, 20000 samples, FP32) in
+    the launch configuration the benchmark times: sampled outputs, plus the
+    ten injected pulses."""
+    s = synth.setup("cfg2")
+    sh = oracle.shift_table(s.freqs(), s.f_ref, s.t_samp, s.dms())
+    pulses = synth.pulse_plan(s, 2, n_per_beam=10)
+    x = synth.make_input(s, sh, seed=2, pulses=pulses)
+    w = synth.make_weights(s.n_chan, 2, "ones")
+    plan = Plan.from_setup(s)
+    out = plan.execute(to_dev(x, "f32"), weights_dev(w, "f32"))
+    torch.cuda.synchronize()
+    rng = np.random.default_rng(22)
+    n = 4000
+    pd = np.concatenate([rng.integers(0, s.n_dm, n), [p[1] for p in pulses],
+                         [0, s.n_dm - 1, s.n_dm - 1, 0]])
+    pt = np.concatenate([rng.integers(0, s.n_out, n), [p[2] for p in pulses],
+                         [0, s.n_out - 1, 0, s.n_out - 1]])
+    pb = np.zeros_like(pd)
+    ref, ab = oracle.forward_points(x, w, sh, pb, pd, pt)
+    got = out[0][torch.from_numpy(pd).cuda(), torch.from_numpy(pt).cuda()].cpu().numpy()
+    assert_float_parity(got, ref, ab, what="cfg2 sampled")
+    # each pulse is recovered at its own trial and time
+    for (_, d, t0, a) in pulses:
+        col = out[0, :, t0].cpu().numpy()
+        assert col[d] > 0.5 * a * s.n_chan
+    plan.check_device()

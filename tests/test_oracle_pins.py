@@ -210,6 +210,16 @@ def test_forward_u8_matches_exact_integer_sum_and_constant():
     assert (oracle.forward_u8(const, wq, sh, S) == 255 * wq.sum()).all()
 
 
+def test_forward_points_u8_agree_with_full():
+    rng = np.random.default_rng(12)
+    sh = np.sort(rng.integers(0, 30, size=(5, 7)), axis=0)
+    x = rng.integers(0, 256, size=(3, 7, synth.padded_stride(20 + 30, "u8"))).astype(np.uint8)
+    wq = rng.integers(-5, 400, size=7)
+    full = oracle.forward_u8(x, wq, sh, 20)
+    pb, pd, pt = rng.integers(0, 3, 50), rng.integers(0, 5, 50), rng.integers(0, 20, 50)
+    np.testing.assert_array_equal(oracle.forward_points_u8(x, wq, sh, pb, pd, pt), full[pb, pd, pt])
+
+
 def test_forward_points_agree_with_full():
     rng = np.random.default_rng(2)
     sh, x, w, stride = _rand_case(rng, B=3, C=6, D=5, S=10, max_shift=7)
