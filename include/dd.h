@@ -160,6 +160,25 @@ dd_status dd_execute_host(dd_plan plan, const void *h_in, const void *h_w, void 
 dd_status dd_adjoint(dd_plan plan, const float *d_gout, const float *d_w,
                      const float *d_in, float *d_gin, float *d_gw, void *stream);
 
+/* ---- Weight gradient without device allocation ---------------------------
+ * The paper has no counterpart to this entry point; it exists for callers
+ * that cannot allocate device memory at the moment they need the gradient
+ * (a caching allocator already holding all free memory, real-time code that
+ * must not take allocator locks or trigger the implicit synchronisation of
+ * cudaMalloc/cudaFree, a device memory budget fixed at start-up).
+ * Computes the same d_gw[c] as dd_adjoint (FP32 plans only) from d_gout
+ * [B][D][S] and d_in [B][C][stride], and allocates nothing: its partial sums
+ * go to one fixed 1 MiB array in the library's device image, which every GPU
+ * that loads the library holds until the process exits. Limits: n_chan <=
+ * 4096 (DD_ERR_ARG beyond). The first call on a device looks up that array's
+ * address with the device current; make that first call before any stream
+ * capture. Every call on a device shares the array and leaves its partial
+ * sums there (each call overwrites all it reads), so calls that may overlap
+ * on the GPU (different streams without ordering) race and must not be
+ * issued. Deterministic: same inputs, same bits. */
+dd_status dd_grad_w_noalloc(dd_plan plan, const float *d_gout, const float *d_in,
+                            float *d_gw, void *stream);
+
 /* ---- Auto-tuning (Section IV-A / V-A) ------------------------------------
  * Times every compiled variant that fits this plan on scratch buffers it
  * allocates and frees itself, keeps the fastest as the plan's variant and

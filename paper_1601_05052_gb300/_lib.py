@@ -67,6 +67,7 @@ SIGNATURES = [
     ("dd_execute", i32, [P, P, P, P, P]),
     ("dd_execute_host", i32, [P, P, P, P, P]),
     ("dd_adjoint", i32, [P, P, P, P, P, P, P]),
+    ("dd_grad_w_noalloc", i32, [P, P, P, P, P]),
     ("dd_tune", i32, [P, i32, ctypes.POINTER(TuneReport)]),
     ("dd_batch_create", i32, [ctypes.POINTER(P), i32, PP]),
     ("dd_batch_execute", i32, [P, PP, PP, PP, P]),
