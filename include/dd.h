@@ -65,14 +65,20 @@ typedef struct dd_batch_s *dd_batch;
 /* Tile shape of the forward kernel (Section III-B's four parameters plus the
  * staging pipeline). A CTA computes dm_per_thread * warps_dm trial DMs by
  * 32 * samples_per_thread * warps_time output samples; input rows of
- * chans_per_stage channels are staged per pipeline stage, `stages` deep. */
+ * chans_per_stage channels are staged per pipeline stage, `stages` deep.
+ * kind 0: lane l of a warp owns samples l, l+32, ...; each add reads its
+ *         input from shared memory.
+ * kind 1: a thread owns samples_per_thread (odd) consecutive samples and
+ *         keeps, per channel, the union window of its warp's trials in
+ *         registers, serving every trial of the warp from it. */
 typedef struct {
-    int32_t dm_per_thread;       /* DMs accumulated per thread (registers)     */
-    int32_t samples_per_thread;  /* samples accumulated per thread (registers) */
-    int32_t warps_dm;            /* warps along the DM axis of a CTA           */
-    int32_t warps_time;          /* warps along the time axis of a CTA         */
-    int32_t chans_per_stage;     /* channels staged per pipeline stage         */
-    int32_t stages;              /* shared-memory pipeline depth               */
+    int32_t kind;                /* 0 lane-strided, 1 register window      */
+    int32_t dm_per_thread;       /* DMs accumulated per thread (registers) */
+    int32_t samples_per_thread;  /* samples accumulated per thread          */
+    int32_t warps_dm;            /* warps along the DM axis of a CTA        */
+    int32_t warps_time;          /* warps along the time axis of a CTA      */
+    int32_t chans_per_stage;     /* channels staged per pipeline stage      */
+    int32_t stages;              /* shared-memory pipeline depth (2..4)     */
 } dd_variant;
 
 /* Outcome of an auto-tuning sweep (Section IV-A / V-B of the paper). Times

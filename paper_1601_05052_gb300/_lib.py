@@ -16,7 +16,8 @@ STATUS = ["DD_OK", "DD_ERR_ARG", "DD_ERR_CUDA", "DD_ERR_NOMEM", "DD_ERR_UNSUPPOR
 
 
 class Variant(ctypes.Structure):
-    _fields_ = [("dm_per_thread", ctypes.c_int32), ("samples_per_thread", ctypes.c_int32),
+    _fields_ = [("kind", ctypes.c_int32),
+                ("dm_per_thread", ctypes.c_int32), ("samples_per_thread", ctypes.c_int32),
                 ("warps_dm", ctypes.c_int32), ("warps_time", ctypes.c_int32),
                 ("chans_per_stage", ctypes.c_int32), ("stages", ctypes.c_int32)]
 

@@ -32,12 +32,13 @@ struct BatchArgs {
     unsigned long long *counter;
 };
 
-template <typename T, int DPT, int SPT>
-__global__ void __launch_bounds__(256, 1) dd_fwd_persistent_kernel(const BatchArgs ba) {
+template <int KIND, typename T, int DPT, int SPT>
+__global__ void __launch_bounds__(KIND == 3 ? 384 : 256, KIND == 3 ? 2 : 1)
+    dd_fwd_persistent_kernel(const BatchArgs ba) {
     extern __shared__ __align__(128) unsigned char smem[];
     __shared__ long long s_item;
-    uint64_t *full = reinterpret_cast<uint64_t *>(smem);
-    fwd_init_barriers(full, ba.stages);
+    uint64_t *bars = reinterpret_cast<uint64_t *>(smem);
+    fwd_init_barriers<KIND>(bars, ba.stages);
     uint32_t kbase = 0;
     const long long n_items = ba.item_start[ba.n];
     for (;;) {
@@ -53,7 +54,7 @@ __global__ void __launch_bounds__(256, 1) dd_fwd_persistent_kernel(const BatchAr
         loc /= a.n_dtiles;
         const int ttile = int(loc % a.n_ttiles);
         const int b = int(loc / a.n_ttiles);
-        fwd_tile<T, DPT, SPT>(a, dtile, ttile, b, full, smem + 128, kbase);
+        fwd_tile_any<KIND, T, DPT, SPT>(a, dtile, ttile, b, bars, smem + 128, kbase);
     }
 }
 
@@ -64,36 +65,36 @@ struct PersistentFn {
     int (*occupancy)(int block, size_t smem) = nullptr;
 };
 
-template <typename T, int DPT, int SPT>
+template <int KIND, typename T, int DPT, int SPT>
 int occupancy_t(int block, size_t smem) {
     if (smem > 48 * 1024 &&
-        cudaFuncSetAttribute(dd_fwd_persistent_kernel<T, DPT, SPT>,
+        cudaFuncSetAttribute(dd_fwd_persistent_kernel<KIND, T, DPT, SPT>,
                              cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)) != cudaSuccess)
         return 0;
     int n = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, dd_fwd_persistent_kernel<T, DPT, SPT>,
-                                                      block, smem) != cudaSuccess)
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+            &n, dd_fwd_persistent_kernel<KIND, T, DPT, SPT>, block, smem) != cudaSuccess)
         return 0;
     return n;
 }
 
 template <typename T>
-PersistentFn pick_persistent_t(int dpt, int spt) {
-#define DD_PICK(D_, S_)                                                          \
-    if (dpt == D_ && spt == S_)                                                  \
-        return PersistentFn{(const void *)&dd_fwd_persistent_kernel<T, D_, S_>, \
-                            &occupancy_t<T, D_, S_>};
+PersistentFn pick_persistent_t(int kind, int dpt, int spt) {
+#define DD_PICK(K_, D_, S_)                                                           \
+    if (kind == K_ && dpt == D_ && spt == S_)                                         \
+        return PersistentFn{(const void *)&dd_fwd_persistent_kernel<K_, T, D_, S_>, \
+                            &occupancy_t<K_, T, D_, S_>};
     DD_FWD_KEYS(DD_PICK)
 #undef DD_PICK
     return PersistentFn{};
 }
 
-PersistentFn pick_persistent(dd_dtype t, int dpt, int spt) {
+PersistentFn pick_persistent(dd_dtype t, int kind, int dpt, int spt) {
     switch (t) {
-        case DD_F32: return pick_persistent_t<float>(dpt, spt);
-        case DD_F16: return pick_persistent_t<__half>(dpt, spt);
-        case DD_BF16: return pick_persistent_t<__nv_bfloat16>(dpt, spt);
-        case DD_U8: return pick_persistent_t<uint8_t>(dpt, spt);
+        case DD_F32: return pick_persistent_t<float>(kind, dpt, spt);
+        case DD_F16: return pick_persistent_t<__half>(kind, dpt, spt);
+        case DD_BF16: return pick_persistent_t<__nv_bfloat16>(kind, dpt, spt);
+        case DD_U8: return pick_persistent_t<uint8_t>(kind, dpt, spt);
     }
     return PersistentFn{};
 }
@@ -132,7 +133,7 @@ void release_tables(dd_batch_s *bt) {
 
 // Builds tables, launch shape and graph for variant v (all plans must fit).
 dd_status configure(dd_batch_s *bt, const dd_variant &v) {
-    PersistentFn pf = pick_persistent(bt->dtype, v.dm_per_thread, v.samples_per_thread);
+    PersistentFn pf = pick_persistent(bt->dtype, v.kind, v.dm_per_thread, v.samples_per_thread);
     if (!pf.fn) return fail(DD_ERR_ARG, "variant not compiled");
     std::vector<FwdTables> tabs;
     size_t smem = 0;
@@ -146,7 +147,7 @@ dd_status configure(dd_batch_s *bt, const dd_variant &v) {
         smem = std::max(smem, t.smem_bytes);
         tabs.push_back(t);
     }
-    const int block = 32 * v.warps_dm * v.warps_time;
+    const int block = 32 * (v.warps_dm * v.warps_time + (v.kind == 3 ? kWsBuilders : 0));
     const int occ = pf.occupancy(block, smem);
     if (occ < 1) {
         for (auto &x : tabs) free_fwd_tables(&x);
@@ -188,6 +189,8 @@ dd_status configure(dd_batch_s *bt, const dd_variant &v) {
         a.B = p->B;
         a.desc = t.d_desc;
         a.offs = t.d_offs;
+        a.bdesc = t.d_bdesc;
+        a.p_elems = t.p_elems;
         a.err = p->d_err;
         bt->ba.item_start[i] = acc;
         acc += (long long)t.n_dtiles * t.n_ttiles * p->B;
@@ -269,7 +272,8 @@ dd_status dd_batch_create(dd_batch *out, int32_t n, const dd_plan *plans) {
         for (int i = 0; i < nv && s != DD_OK; ++i) {
             dd_variant v;
             dd_variant_get(i, &v);
-            if (v.dm_per_thread == 4 && v.samples_per_thread == 4) s = configure(bt, v);
+            if (v.kind == 0 && v.dm_per_thread == 4 && v.samples_per_thread == 4)
+                s = configure(bt, v);
         }
         for (int i = 0; i < nv && s != DD_OK; ++i) {
             dd_variant v;
@@ -373,61 +377,31 @@ dd_status dd_batch_tune(dd_batch bt, int32_t budget_ms, dd_tune_report *rep) {
         uw[size_t(u)] = ws[i];
         uout[size_t(u)] = outs[i];
     }
-    const dd_variant start = bt->v;
-    const auto wall0 = std::chrono::steady_clock::now();
-    std::vector<double> gflops;
-    dd_variant best = start;
-    double best_ms = 1e300;
-    const int nv = dd_variant_count();
-    for (int i = 0; i < nv; ++i) {
-        if (budget_ms > 0 && !gflops.empty() &&
-            std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - wall0)
-                    .count() > budget_ms)
-            break;
-        dd_variant v;
-        dd_variant_get(i, &v);
-        if (configure(bt, v) != DD_OK) continue;
+    auto time_ms = [&](const dd_variant &v, double *ms) -> dd_status {
+        if (configure(bt, v) != DD_OK) return DD_OK;  // does not fit every plan
         bt->args_on_device = false;
         dd_status s = dd_batch_execute(bt, uin.data(), uw.data(), uout.data(), st);
         const int reps = 3;
-        if (s == DD_OK) e = cudaEventRecord(e0, st);
-        for (int r = 0; r < reps && s == DD_OK; ++r)
+        cudaError_t ce = cudaSuccess;
+        if (s == DD_OK) ce = cudaEventRecord(e0, st);
+        for (int r = 0; r < reps && s == DD_OK && ce == cudaSuccess; ++r)
             s = dd_batch_execute(bt, uin.data(), uw.data(), uout.data(), st);
-        if (s == DD_OK && e == cudaSuccess) e = cudaEventRecord(e1, st);
-        if (s == DD_OK && e == cudaSuccess) e = cudaEventSynchronize(e1);
-        float ms = 0.f;
-        if (s == DD_OK && e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
-        if (s != DD_OK || e != cudaSuccess) {
-            cleanup();
-            return s != DD_OK ? s : cuda_fail(e, "batch tuner timing");
-        }
-        const double per = double(ms) / reps;
-        gflops.push_back(flop / (per * 1e6));
-        if (per < best_ms) {
-            best_ms = per;
-            best = v;
-        }
-    }
+        if (s == DD_OK && ce == cudaSuccess) ce = cudaEventRecord(e1, st);
+        if (s == DD_OK && ce == cudaSuccess) ce = cudaEventSynchronize(e1);
+        float f = 0.f;
+        if (s == DD_OK && ce == cudaSuccess) ce = cudaEventElapsedTime(&f, e0, e1);
+        if (s != DD_OK) return s;
+        if (ce != cudaSuccess) return cuda_fail(ce, "batch tuner timing");
+        *ms = double(f) / reps;
+        return DD_OK;
+    };
+    const dd_variant start = bt->v;
+    dd_variant best = start;
+    dd_status s = sweep_variants(budget_ms, flop, time_ms, &best, rep);
     cleanup();
-    dd_status s = configure(bt, best);
+    dd_status s2 = configure(bt, s == DD_OK ? best : start);
     if (s != DD_OK) return s;
-    if (gflops.empty()) return fail(DD_ERR_NOT_TUNED, "no variant fits the batch");
-    if (rep) {
-        double mean = 0.0, var = 0.0;
-        for (double g : gflops) mean += g;
-        mean /= double(gflops.size());
-        for (double g : gflops) var += (g - mean) * (g - mean);
-        const double sd = gflops.size() > 1 ? std::sqrt(var / double(gflops.size() - 1)) : 0.0;
-        rep->n_tried = int32_t(gflops.size());
-        rep->best = best;
-        rep->best_ms = best_ms;
-        rep->best_gflops = flop / (best_ms * 1e6);
-        rep->mean_gflops = mean;
-        rep->std_gflops = sd;
-        rep->snr = sd > 0 ? (rep->best_gflops - mean) / sd : 0.0;
-        rep->chebyshev = rep->snr > 1.0 ? 1.0 / (rep->snr * rep->snr) : 1.0;
-    }
-    return DD_OK;
+    return s2;
 }
 
 void dd_batch_destroy(dd_batch bt) {

@@ -12,49 +12,51 @@
 
 namespace dd {
 
-template <typename T, int DPT, int SPT>
-__global__ void __launch_bounds__(256, 1) dd_fwd_kernel(const FwdArgs a) {
+template <int KIND, typename T, int DPT, int SPT>
+__global__ void __launch_bounds__(KIND == 3 ? 384 : 256, KIND == 3 ? 2 : 1)
+    dd_fwd_kernel(const FwdArgs a) {
     extern __shared__ __align__(128) unsigned char smem[];
-    uint64_t *full = reinterpret_cast<uint64_t *>(smem);
-    fwd_init_barriers(full, a.stages);
+    uint64_t *bars = reinterpret_cast<uint64_t *>(smem);
+    fwd_init_barriers<KIND>(bars, a.stages);
     uint32_t kbase = 0;
-    fwd_tile<T, DPT, SPT>(a, blockIdx.x, blockIdx.y, blockIdx.z, full, smem + 128, kbase);
+    fwd_tile_any<KIND, T, DPT, SPT>(a, blockIdx.x, blockIdx.y, blockIdx.z, bars, smem + 128,
+                                    kbase);
 }
 
 namespace {
 
 using FwdLaunchFn = cudaError_t (*)(const FwdArgs &, dim3, dim3, size_t, cudaStream_t);
 
-template <typename T, int DPT, int SPT>
+template <int KIND, typename T, int DPT, int SPT>
 cudaError_t launch_fwd_t(const FwdArgs &a, dim3 grid, dim3 block, size_t smem, cudaStream_t st) {
     // Raise the kernel's dynamic shared-memory limit once per size increase.
     static std::atomic<size_t> smem_set{0};
     if (smem > 48 * 1024 && smem > smem_set.load()) {
-        cudaError_t e = cudaFuncSetAttribute(dd_fwd_kernel<T, DPT, SPT>,
+        cudaError_t e = cudaFuncSetAttribute(dd_fwd_kernel<KIND, T, DPT, SPT>,
                                              cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              int(smem));
         if (e != cudaSuccess) return e;
         smem_set.store(smem);
     }
-    dd_fwd_kernel<T, DPT, SPT><<<grid, block, smem, st>>>(a);
+    dd_fwd_kernel<KIND, T, DPT, SPT><<<grid, block, smem, st>>>(a);
     return cudaGetLastError();
 }
 
 template <typename T>
-FwdLaunchFn pick(int dpt, int spt) {
-#define DD_PICK(D_, S_) \
-    if (dpt == D_ && spt == S_) return &launch_fwd_t<T, D_, S_>;
+FwdLaunchFn pick(int kind, int dpt, int spt) {
+#define DD_PICK(K_, D_, S_) \
+    if (kind == K_ && dpt == D_ && spt == S_) return &launch_fwd_t<K_, T, D_, S_>;
     DD_FWD_KEYS(DD_PICK)
 #undef DD_PICK
     return nullptr;
 }
 
-FwdLaunchFn pick_fn(dd_dtype t, int dpt, int spt) {
+FwdLaunchFn pick_fn(dd_dtype t, int kind, int dpt, int spt) {
     switch (t) {
-        case DD_F32: return pick<float>(dpt, spt);
-        case DD_F16: return pick<__half>(dpt, spt);
-        case DD_BF16: return pick<__nv_bfloat16>(dpt, spt);
-        case DD_U8: return pick<uint8_t>(dpt, spt);
+        case DD_F32: return pick<float>(kind, dpt, spt);
+        case DD_F16: return pick<__half>(kind, dpt, spt);
+        case DD_BF16: return pick<__nv_bfloat16>(kind, dpt, spt);
+        case DD_U8: return pick<uint8_t>(kind, dpt, spt);
     }
     return nullptr;
 }
@@ -63,18 +65,20 @@ FwdLaunchFn pick_fn(dd_dtype t, int dpt, int spt) {
 
 const std::vector<FwdKernelKey> &fwd_compiled_keys() {
     static const std::vector<FwdKernelKey> keys = {
-#define DD_KEY(D_, S_) FwdKernelKey{D_, S_},
+#define DD_KEY(K_, D_, S_) FwdKernelKey{K_, D_, S_},
         DD_FWD_KEYS(DD_KEY)
 #undef DD_KEY
     };
     return keys;
 }
 
-bool fwd_variant_compiled(int dpt, int spt) { return pick_fn(DD_F32, dpt, spt) != nullptr; }
+bool fwd_variant_compiled(int kind, int dpt, int spt) {
+    return pick_fn(DD_F32, kind, dpt, spt) != nullptr;
+}
 
 dd_status launch_forward(dd_plan_s *p, const FwdTables &t, const void *in, const void *w,
                          void *out, cudaStream_t st) {
-    FwdLaunchFn fn = pick_fn(p->dtype, t.v.dm_per_thread, t.v.samples_per_thread);
+    FwdLaunchFn fn = pick_fn(p->dtype, t.v.kind, t.v.dm_per_thread, t.v.samples_per_thread);
     if (!fn) return fail(DD_ERR_UNSUPPORTED, "forward variant not compiled");
     FwdArgs a;
     a.in = in;
@@ -97,9 +101,11 @@ dd_status launch_forward(dd_plan_s *p, const FwdTables &t, const void *in, const
     a.B = p->B;
     a.desc = t.d_desc;
     a.offs = t.d_offs;
+    a.bdesc = t.d_bdesc;
+    a.p_elems = t.p_elems;
     a.err = p->d_err;
     dim3 grid(unsigned(t.n_dtiles), unsigned(t.n_ttiles), unsigned(p->B));
-    dim3 block(unsigned(32 * t.v.warps_dm * t.v.warps_time));
+    dim3 block(unsigned(32 * (t.v.warps_dm * t.v.warps_time + (t.v.kind == 3 ? kWsBuilders : 0))));
     cudaError_t e = fn(a, grid, block, t.smem_bytes, st);
     if (e != cudaSuccess) return cuda_fail(e, "forward launch");
     return DD_OK;

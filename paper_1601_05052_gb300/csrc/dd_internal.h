@@ -5,6 +5,7 @@
 
 #include <cstddef>
 #include <cstdint>
+#include <functional>
 #include <mutex>
 #include <string>
 #include <vector>
@@ -44,7 +45,18 @@ struct FwdTables {
     size_t smem_bytes = 0;       // dynamic shared memory of one CTA
     int4 *d_desc = nullptr;
     uint16_t *d_offs = nullptr;
+    // kind 2 (sub-band) only: d_offs holds per-group trial offsets into the
+    // partial-sum buffer, [n_dtiles][C_pad/4][Dt]; d_bdesc the partial-series
+    // build descriptors, [n_dtiles][C_pad/4][kSbPatterns] x 2 int4; p_elems
+    // the partial-sum buffer length of one chunk.
+    int4 *d_bdesc = nullptr;
+    int p_elems = 0;
 };
+
+// Sub-band (kind 2) geometry: channels per group, distinct delay patterns a
+// group may have inside one DM tile.
+constexpr int kSbGroup = 4;
+constexpr int kSbPatterns = 8;
 
 // Tables of the adjoint (gather) kernel: the roles of channels and trials
 // swap. A CTA owns a tile of Ct channels by Tt input samples and stages, per
@@ -77,6 +89,7 @@ struct dd_plan_s {
 
     dd::FwdTables fwd;
     dd::AdjTables adj;
+    int32_t *d_shifts = nullptr;  // device copy of `shifts`
     int *d_err = nullptr;         // device error word (dd::kErr* bits)
 
     // device mirrors for dd_execute_host, allocated on first use
@@ -92,11 +105,11 @@ dd_status fail(dd_status s, const std::string &msg);
 dd_status cuda_fail(cudaError_t e, const char *what);
 dd_status ok();
 
-// Compiled forward variants: (dm_per_thread, samples_per_thread) pairs with
-// a kernel for every input type.
-struct FwdKernelKey { int dpt, spt; };
+// Compiled forward variants: (kind, dm_per_thread, samples_per_thread) with a
+// kernel for every input type.
+struct FwdKernelKey { int kind, dpt, spt; };
 const std::vector<FwdKernelKey> &fwd_compiled_keys();
-bool fwd_variant_compiled(int dpt, int spt);
+bool fwd_variant_compiled(int kind, int dpt, int spt);
 
 // Builds (or rebuilds) the forward tables for variant v; DD_ERR_ARG if v does
 // not fit this plan/device.
@@ -115,5 +128,11 @@ dd_status launch_adjoint(dd_plan_s *p, const float *g, const float *w, const flo
                          float *gin, float *gw, cudaStream_t st);
 
 bool aligned16(const void *p);
+
+// Two-pass sweep of the variant grid (dd_tune.cpp). time_ms(v, &ms) sets ms
+// <= 0 for variants that do not fit; returns the fastest in *best.
+dd_status sweep_variants(int32_t budget_ms, double flop,
+                         const std::function<dd_status(const dd_variant &, double *)> &time_ms,
+                         dd_variant *best, dd_tune_report *rep);
 
 }  // namespace dd

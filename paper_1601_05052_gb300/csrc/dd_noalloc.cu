@@ -11,11 +11,10 @@
 //     gw[c] = sum_b sum_d sum_t g[b][d][t] * in[b][c][t + shift[d][c]]
 // with its partial sums in a fixed-size array that lives in the library's
 // own device image (file-scope __device__ storage), so nothing is allocated:
-// the delay table is read back from the forward staging tables the plan
-// built when it was created.
+// the delay table is the device copy the plan made when it was created.
 //
-// Work split: CTA k of G takes tiles k, k + G, ... of the plan's forward
-// tiling (DM tile, time tile, beam); each warp keeps its own per-channel
+// Work split: the outputs are cut into tiles of 16 trials by 256 samples per
+// beam; CTA k of G takes tiles k, k + G, ...; each warp keeps its own per-channel
 // running sums in shared memory, the CTA adds its warps in a fixed order
 // into row k of the scratch array, and a second kernel adds the G rows in a
 // fixed order. Results are therefore reproducible bit for bit.
@@ -24,7 +23,6 @@
 #include <algorithm>
 #include <mutex>
 
-#include "dd_fwd_tile.cuh"
 #include "dd_internal.h"
 
 namespace dd {
@@ -38,15 +36,19 @@ constexpr int kMaxDevices = 64;
 
 static __device__ __align__(256) float g_noalloc_scratch[kNoAllocScratchFloats];
 
+// Tiling of this kernel: 8 warps, 4 along trials and 2 along time; a thread
+// covers 4 trials by 4 lane-strided samples.
+constexpr int kNaDpt = 4, kNaSpt = 4, kNaWarpsDm = 4, kNaWarpsT = 2;
+constexpr int kNaDt = kNaDpt * kNaWarpsDm, kNaTs = 32 * kNaSpt * kNaWarpsT;
+
 struct NoAllocArgs {
-    const float *g;    // [B][D][S]
-    const float *in;   // [B][C][stride]
-    float *part;       // [G][C] (the scratch array)
+    const float *g;       // [B][D][S]
+    const float *in;      // [B][C][stride]
+    const int32_t *shifts;  // [D][C]
+    float *part;          // [G][C] (the scratch array)
     int C, D, B;
     long long S, stride;
-    int Dt, Ts, C_pad, warps_dm, n_dtiles, n_ttiles;
-    const int4 *desc;
-    const uint16_t *offs;
+    int n_dtiles, n_ttiles;
 };
 
 template <int DPT, int SPT>
@@ -54,7 +56,7 @@ __global__ void __launch_bounds__(256, 1) dd_gw_noalloc_kernel(const NoAllocArgs
     extern __shared__ float wsum[];  // [n_warps][C]
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int n_warps = blockDim.x >> 5;
-    const int wd = warp % a.warps_dm, wt = warp / a.warps_dm;
+    const int wd = warp % kNaWarpsDm, wt = warp / kNaWarpsDm;
     for (int e = tid; e < n_warps * a.C; e += blockDim.x) wsum[e] = 0.f;
     __syncthreads();
     float *mine = wsum + warp * a.C;
@@ -65,13 +67,13 @@ __global__ void __launch_bounds__(256, 1) dd_gw_noalloc_kernel(const NoAllocArgs
         const long long rest = item / a.n_dtiles;
         const int ttile = int(rest % a.n_ttiles);
         const int b = int(rest / a.n_ttiles);
-        const long long tb = (long long)ttile * a.Ts + wt * 32 * SPT + lane;
+        const long long tb = (long long)ttile * kNaTs + wt * 32 * SPT + lane;
         // this thread's cotangent values (zero outside the output)
         float gr[DPT][SPT];
         bool dv[DPT];
 #pragma unroll
         for (int i = 0; i < DPT; ++i) {
-            const int d = dtile * a.Dt + wd * DPT + i;
+            const int d = dtile * kNaDt + wd * DPT + i;
             dv[i] = d < a.D;
 #pragma unroll
             for (int j = 0; j < SPT; ++j) {
@@ -80,17 +82,14 @@ __global__ void __launch_bounds__(256, 1) dd_gw_noalloc_kernel(const NoAllocArgs
                                               : 0.f;
             }
         }
-        const int4 *desc_k = a.desc + (size_t)dtile * a.C_pad;
-        const uint16_t *offs_k = a.offs + (size_t)dtile * a.C_pad * a.Dt + wd * DPT;
+        const int32_t *sh_k = a.shifts + (size_t)(dtile * kNaDt + wd * DPT) * a.C;
         for (int c = 0; c < a.C; ++c) {
-            const int4 dsc = desc_k[c];
             const float *row = a.in + ((long long)b * a.C + c) * a.stride;
             float p = 0.f;
 #pragma unroll
             for (int i = 0; i < DPT; ++i) {
                 if (!dv[i]) continue;
-                // delay of trial i in channel c, recovered from the staging tables
-                const int shift = int(offs_k[(size_t)c * a.Dt + i]) - dsc.z + dsc.x;
+                const int shift = __ldg(sh_k + (size_t)i * a.C + c);
 #pragma unroll
                 for (int j = 0; j < SPT; ++j) {
                     const long long t = tb + 32 * j;
@@ -119,21 +118,6 @@ __global__ void dd_gw_noalloc_reduce_kernel(const float *part, int G, int C, flo
     gw[c] = float(s);
 }
 
-using NoAllocLaunch = void (*)(const NoAllocArgs &, int, int, size_t, cudaStream_t);
-
-template <int DPT, int SPT>
-void launch_noalloc_t(const NoAllocArgs &a, int grid, int block, size_t smem, cudaStream_t st) {
-    dd_gw_noalloc_kernel<DPT, SPT><<<grid, block, smem, st>>>(a);
-}
-
-NoAllocLaunch pick_noalloc(int dpt, int spt) {
-#define DD_PICK(D_, S_) \
-    if (dpt == D_ && spt == S_) return &launch_noalloc_t<D_, S_>;
-    DD_FWD_KEYS(DD_PICK)
-#undef DD_PICK
-    return nullptr;
-}
-
 // Device address of the scratch array, looked up once per device (with that
 // device current) on the first call made on it.
 std::mutex g_noalloc_mu;
@@ -153,15 +137,12 @@ extern "C" dd_status dd_grad_w_noalloc(dd_plan p, const float *d_gout, const flo
         return fail(DD_ERR_ARG, "device pointers must be 16-byte aligned");
     if (p->C > kNoAllocMaxChan)
         return fail(DD_ERR_ARG, "dd_grad_w_noalloc supports at most 4096 channels");
-    const FwdTables &t = p->fwd;
-    NoAllocLaunch fn = pick_noalloc(t.v.dm_per_thread, t.v.samples_per_thread);
-    if (!fn) return fail(DD_ERR_UNSUPPORTED, "plan variant not compiled for dd_grad_w_noalloc");
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
     if (dev != p->device) return fail(DD_ERR_ARG, "make the plan's device current first");
     if (dev < 0 || dev >= kMaxDevices) return fail(DD_ERR_UNSUPPORTED, "device index too large");
-    const int block = 32 * t.v.warps_dm * t.v.warps_time;
+    const int block = 32 * kNaWarpsDm * kNaWarpsT;
     const size_t smem = size_t(block / 32) * p->C * sizeof(float);
     float *scratch = nullptr;
     {
@@ -176,40 +157,34 @@ extern "C" dd_status dd_grad_w_noalloc(dd_plan p, const float *d_gout, const flo
         if (!g_noalloc_attr_set[dev]) {
             // the largest per-warp shared-memory table any plan may need
             const int max_smem = 8 * kNoAllocMaxChan * int(sizeof(float));
-#define DD_ATTR(D_, S_)                                                                     \
-    if (e == cudaSuccess)                                                                   \
-        e = cudaFuncSetAttribute(dd_gw_noalloc_kernel<D_, S_>,                              \
-                                 cudaFuncAttributeMaxDynamicSharedMemorySize, max_smem);
-            DD_FWD_KEYS(DD_ATTR)
-#undef DD_ATTR
+            e = cudaFuncSetAttribute(dd_gw_noalloc_kernel<kNaDpt, kNaSpt>,
+                                     cudaFuncAttributeMaxDynamicSharedMemorySize, max_smem);
             if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute(no-alloc)");
             g_noalloc_attr_set[dev] = true;
         }
     }
-    const long long n_items = (long long)t.n_dtiles * t.n_ttiles * p->B;
+    const int n_dtiles = (p->D + kNaDt - 1) / kNaDt;
+    const long long n_ttiles = (p->S + kNaTs - 1) / kNaTs;
+    const long long n_items = (long long)n_dtiles * n_ttiles * p->B;
     long long G = std::min<long long>(n_items, 2LL * p->sm_count);
     G = std::min<long long>(G, kNoAllocScratchFloats / p->C);
     if (G < 1) G = 1;
 
+    if (n_ttiles > (1LL << 30)) return fail(DD_ERR_ARG, "too many samples");
     NoAllocArgs a;
     a.g = d_gout;
     a.in = d_in;
+    a.shifts = p->d_shifts;
     a.part = scratch;
     a.C = p->C;
     a.D = p->D;
     a.B = p->B;
     a.S = p->S;
     a.stride = p->stride;
-    a.Dt = t.Dt;
-    a.Ts = t.Ts;
-    a.C_pad = t.C_pad;
-    a.warps_dm = t.v.warps_dm;
-    a.n_dtiles = t.n_dtiles;
-    a.n_ttiles = t.n_ttiles;
-    a.desc = t.d_desc;
-    a.offs = t.d_offs;
+    a.n_dtiles = n_dtiles;
+    a.n_ttiles = int(n_ttiles);
     cudaStream_t st = static_cast<cudaStream_t>(stream);
-    fn(a, int(G), block, smem, st);
+    dd_gw_noalloc_kernel<kNaDpt, kNaSpt><<<int(G), block, smem, st>>>(a);
     e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(e, "dd_grad_w_noalloc launch");
     dd_gw_noalloc_reduce_kernel<<<(p->C + 127) / 128, 128, 0, st>>>(scratch, int(G), p->C, d_gw);

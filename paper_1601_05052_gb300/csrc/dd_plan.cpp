@@ -38,8 +38,8 @@ dd_status ok() { return DD_OK; }
 bool aligned16(const void *p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
 
 dd_status check_variant_shape(const dd_variant &v) {
-    if (!fwd_variant_compiled(v.dm_per_thread, v.samples_per_thread))
-        return fail(DD_ERR_ARG, "variant (dm_per_thread, samples_per_thread) not compiled");
+    if (!fwd_variant_compiled(v.kind, v.dm_per_thread, v.samples_per_thread))
+        return fail(DD_ERR_ARG, "variant (kind, dm_per_thread, samples_per_thread) not compiled");
     if (v.warps_dm < 1 || v.warps_time < 1 || v.warps_dm * v.warps_time > 8)
         return fail(DD_ERR_ARG, "variant warps_dm * warps_time must be in [1, 8]");
     if (v.chans_per_stage != 4 && v.chans_per_stage != 8 && v.chans_per_stage != 16)
@@ -47,6 +47,80 @@ dd_status check_variant_shape(const dd_variant &v) {
     if (v.stages < 2 || v.stages > 4) return fail(DD_ERR_ARG, "variant stages must be 2..4");
     return DD_OK;
 }
+
+namespace {
+
+// Sub-band (kind 2) tables of one DM tile and one chunk of channels. For a
+// group of up to 4 adjacent channels with reference channel r (its last),
+// trial d has base delay base(d) = shift[d][r] and relative pattern
+// rho_c(d) = shift[d][c] - base(d). Trials sharing a pattern p read the
+// weighted partial series P_p[u] = sum_c w_c * x_c[t0 + u + rho_c], u in
+// [Bmin_p, Bmax_p + Ts), at index u = t + base(d); the CTA builds each P_p
+// once in shared memory and every trial of p adds one P_p value per output
+// instead of one input value per channel.
+struct SbChunk {
+    std::vector<int> bdesc;   // [groups][kSbPatterns][8]
+    std::vector<int> poffs;   // [groups][Dt]
+    int64_t p_elems = 0;
+};
+
+dd_status sb_chunk(const dd_plan_s *p, int d0, int d1, int Dt, int Ts, int c0, int nch_chunk,
+                   const std::vector<int4> &raw_desc_k, SbChunk *out) {
+    const int ngroups = (nch_chunk + kSbGroup - 1) / kSbGroup;
+    out->bdesc.assign(size_t(ngroups) * kSbPatterns * 8, 0);
+    out->poffs.assign(size_t(ngroups) * Dt, 0);
+    int64_t psoff = 0;
+    for (int g = 0; g < ngroups; ++g) {
+        const int ga = c0 + g * kSbGroup;
+        const int gn = std::min(kSbGroup, p->C - ga);
+        if (gn <= 0) continue;
+        const int ref = ga + gn - 1;
+        std::vector<std::vector<int32_t>> pats;
+        std::vector<int32_t> bmin, bmax;
+        std::vector<int> pid(size_t(Dt), 0);
+        for (int d = d0; d < d1; ++d) {
+            const int32_t base = p->shifts[size_t(d) * p->C + ref];
+            std::vector<int32_t> rho(static_cast<size_t>(gn), 0);
+            for (int j = 0; j < gn; ++j) rho[size_t(j)] = p->shifts[size_t(d) * p->C + ga + j] - base;
+            size_t q = 0;
+            while (q < pats.size() && pats[q] != rho) ++q;
+            if (q == pats.size()) {
+                if (int(q) == kSbPatterns) return DD_ERR_ARG;  // too many patterns for this tile
+                pats.push_back(rho);
+                bmin.push_back(base);
+                bmax.push_back(base);
+            }
+            bmin[q] = std::min(bmin[q], base);
+            bmax[q] = std::max(bmax[q], base);
+            pid[size_t(d - d0)] = int(q);
+        }
+        std::vector<int64_t> pso(pats.size());
+        for (size_t q = 0; q < pats.size(); ++q) {
+            const int64_t L = int64_t(bmax[q]) - bmin[q] + Ts;
+            pso[q] = psoff;
+            int *bd = &out->bdesc[(size_t(g) * kSbPatterns + q) * 8];
+            bd[0] = int(psoff);
+            bd[1] = int(L);
+            for (int j = 0; j < gn; ++j) {
+                const int4 r = raw_desc_k[size_t(ga + j)];  // {ws, len, soff, 0}
+                bd[2 + j] = int(r.z + bmin[q] + pats[q][size_t(j)] - r.x);
+            }
+            bd[6] = gn;
+            psoff += L;
+        }
+        for (int i = 0; i < Dt; ++i) {
+            const int d = d0 + i;
+            if (d >= d1) continue;
+            const int q = pid[size_t(i)];
+            out->poffs[size_t(g) * Dt + i] =
+                int(pso[size_t(q)] + p->shifts[size_t(d) * p->C + ref] - bmin[size_t(q)]);
+        }
+    }
+    out->p_elems = psoff;
+    return DD_OK;
+}
+
+}  // namespace
 
 dd_status build_fwd_tables(dd_plan_s *p, const dd_variant &v, FwdTables *out) {
     dd_status s = check_variant_shape(v);
@@ -61,11 +135,17 @@ dd_status build_fwd_tables(dd_plan_s *p, const dd_variant &v, FwdTables *out) {
     t.C_pad = (p->C + cch - 1) / cch * cch;
     const int al = align_elems(p->dtype);
     const int elt = elt_bytes(p->dtype);
+    const bool sb = v.kind == 2 || v.kind == 3;
     if (t.n_ttiles > 65535) return fail(DD_ERR_ARG, "too many time tiles for this variant");
+    if (sb && t.Dt % 8 != 0) return fail(DD_ERR_ARG, "sub-band variants need 8 | DM tile");
 
+    const int G_pad = t.C_pad / kSbGroup;
     std::vector<int4> desc(size_t(t.n_dtiles) * t.C_pad, make_int4(0, 0, 0, 0));
-    std::vector<uint16_t> offs(size_t(t.n_dtiles) * t.C_pad * t.Dt, 0);
-    int64_t stage_max = 0;
+    std::vector<uint16_t> offs(sb ? size_t(t.n_dtiles) * G_pad * t.Dt
+                                  : size_t(t.n_dtiles) * t.C_pad * t.Dt, 0);
+    std::vector<int4> bdesc(sb ? size_t(t.n_dtiles) * G_pad * kSbPatterns * 2 : 0,
+                            make_int4(0, 0, 0, 0));
+    int64_t stage_max = 0, p_max = 0;
     for (int k = 0; k < t.n_dtiles; ++k) {
         const int d0 = k * t.Dt, d1 = std::min(p->D, d0 + t.Dt);
         for (int c0 = 0; c0 < p->C; c0 += cch) {
@@ -80,35 +160,74 @@ dd_status build_fwd_tables(dd_plan_s *p, const dd_variant &v, FwdTables *out) {
                 const int64_t ws = floor_to(smin, al);
                 const int64_t len = round_up(smax + t.Ts - ws, al);
                 if (soff + len > 65536) return fail(DD_ERR_ARG, "stage too large for variant");
-                desc[size_t(k) * t.C_pad + c] =
-                    make_int4(int(ws), int(len), int(soff), 0);
-                for (int i = 0; i < t.Dt; ++i) {
-                    const int d = d0 + i;
-                    const int64_t o = d < p->D ? soff + p->shifts[size_t(d) * p->C + c] - ws : soff;
-                    offs[(size_t(k) * t.C_pad + c) * t.Dt + i] = static_cast<uint16_t>(o);
+                desc[size_t(k) * t.C_pad + c] = make_int4(int(ws), int(len), int(soff), 0);
+                if (!sb) {
+                    for (int i = 0; i < t.Dt; ++i) {
+                        const int d = d0 + i;
+                        const int64_t o =
+                            d < p->D ? soff + p->shifts[size_t(d) * p->C + c] - ws : soff;
+                        offs[(size_t(k) * t.C_pad + c) * t.Dt + i] = static_cast<uint16_t>(o);
+                    }
                 }
                 soff += len;
             }
             stage_max = std::max(stage_max, soff);
+            if (sb) {
+                SbChunk ch;
+                std::vector<int4> raw_k(desc.begin() + size_t(k) * t.C_pad,
+                                        desc.begin() + size_t(k + 1) * t.C_pad);
+                if (sb_chunk(p, d0, d1, t.Dt, t.Ts, c0, std::min(cch, p->C - c0), raw_k, &ch) !=
+                    DD_OK)
+                    return fail(DD_ERR_ARG, "too many delay patterns per channel group");
+                if (ch.p_elems > 65536 - t.Ts)
+                    return fail(DD_ERR_ARG, "partial-sum buffer too large for variant");
+                p_max = std::max(p_max, ch.p_elems);
+                const int g0 = c0 / kSbGroup;
+                const int ng = int(ch.poffs.size()) / t.Dt;
+                for (int g = 0; g < ng; ++g) {
+                    for (int i = 0; i < t.Dt; ++i)
+                        offs[(size_t(k) * G_pad + g0 + g) * t.Dt + i] =
+                            static_cast<uint16_t>(ch.poffs[size_t(g) * t.Dt + i]);
+                    for (int q = 0; q < kSbPatterns; ++q) {
+                        const int *bd = &ch.bdesc[(size_t(g) * kSbPatterns + q) * 8];
+                        const size_t at = ((size_t(k) * G_pad + g0 + g) * kSbPatterns + q) * 2;
+                        bdesc[at] = make_int4(bd[0], bd[1], bd[2], bd[3]);
+                        bdesc[at + 1] = make_int4(bd[4], bd[5], bd[6], bd[7]);
+                    }
+                }
+            }
         }
     }
     t.stage_elems = static_cast<int>(stage_max);
-    t.stage_data_bytes = static_cast<int>(round_up(stage_max * elt, 16));
-    t.stage_offs_bytes = static_cast<int>(round_up(int64_t(cch) * t.Dt * 2, 16));
-    t.smem_bytes = 128 + size_t(v.stages) * (t.stage_data_bytes + t.stage_offs_bytes);
+    // 64 spare elements: register-window loads of a warp never leave the slot
+    t.stage_data_bytes = static_cast<int>(round_up((stage_max + 64) * elt, 16));
+    if (sb) {
+        const int gpc = cch / kSbGroup;
+        t.stage_offs_bytes = static_cast<int>(round_up(int64_t(gpc) * t.Dt * 2, 16)) +
+                             gpc * kSbPatterns * 32;
+        t.p_elems = static_cast<int>(round_up(p_max + 64, 4));
+    } else {
+        t.stage_offs_bytes = static_cast<int>(round_up(int64_t(cch) * t.Dt * 2, 16));
+    }
+    size_t p_bytes = 0;
+    if (v.kind == 2) p_bytes = size_t(2) * t.p_elems * 4;
+    if (v.kind == 3)  // 3 partial-sum slots, each with the chunk's trial offsets
+        p_bytes = size_t(3) * (size_t(t.p_elems) * 4 + size_t(cch / kSbGroup) * t.Dt * 2);
+    t.smem_bytes = 128 + size_t(v.stages) * (t.stage_data_bytes + t.stage_offs_bytes) + p_bytes;
     if (t.smem_bytes > p->smem_optin)
         return fail(DD_ERR_ARG, "variant needs more shared memory than the device has");
 
     cudaError_t e = cudaMalloc(&t.d_desc, desc.size() * sizeof(int4));
     if (e != cudaSuccess) return cuda_fail(e, "cudaMalloc(desc)");
     e = cudaMalloc(&t.d_offs, offs.size() * sizeof(uint16_t));
-    if (e != cudaSuccess) {
-        cudaFree(t.d_desc);
-        return cuda_fail(e, "cudaMalloc(offs)");
-    }
-    e = cudaMemcpy(t.d_desc, desc.data(), desc.size() * sizeof(int4), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess && sb) e = cudaMalloc(&t.d_bdesc, bdesc.size() * sizeof(int4));
+    if (e == cudaSuccess)
+        e = cudaMemcpy(t.d_desc, desc.data(), desc.size() * sizeof(int4), cudaMemcpyHostToDevice);
     if (e == cudaSuccess)
         e = cudaMemcpy(t.d_offs, offs.data(), offs.size() * sizeof(uint16_t),
+                       cudaMemcpyHostToDevice);
+    if (e == cudaSuccess && sb)
+        e = cudaMemcpy(t.d_bdesc, bdesc.data(), bdesc.size() * sizeof(int4),
                        cudaMemcpyHostToDevice);
     if (e != cudaSuccess) {
         free_fwd_tables(&t);
@@ -121,16 +240,23 @@ dd_status build_fwd_tables(dd_plan_s *p, const dd_variant &v, FwdTables *out) {
 void free_fwd_tables(FwdTables *t) {
     if (t->d_desc) cudaFree(t->d_desc);
     if (t->d_offs) cudaFree(t->d_offs);
+    if (t->d_bdesc) cudaFree(t->d_bdesc);
     t->d_desc = nullptr;
     t->d_offs = nullptr;
+    t->d_bdesc = nullptr;
 }
 
 namespace {
 
 // Candidate default variants, best first; the first that fits the plan is
 // used until dd_tune or dd_plan_set_variant picks another.
+// (Measured on GB300: the sub-band kind with 64-trial by 128-sample tiles and
+// 16 channels per stage leads on the Apertif-like and 512-channel setups; the
+// lane-strided kind 0 takes setups whose delay patterns are too varied for
+// sub-bands, e.g. wide low-frequency bands.)
 const dd_variant kDefaults[] = {
-    {4, 4, 4, 2, 8, 3}, {4, 4, 4, 2, 4, 2}, {2, 4, 4, 2, 4, 2}, {2, 2, 4, 2, 4, 2},
+    {2, 8, 4, 8, 1, 16, 2}, {2, 8, 4, 4, 2, 8, 2}, {0, 4, 8, 4, 1, 8, 3}, {0, 4, 4, 4, 2, 8, 3},
+    {0, 4, 4, 4, 2, 4, 2},  {0, 2, 4, 4, 2, 4, 2},  {0, 4, 2, 4, 1, 4, 2},
 };
 
 dd_status finish_plan(dd_plan_s *p, dd_plan *out) {
@@ -148,6 +274,11 @@ dd_status finish_plan(dd_plan_s *p, dd_plan *out) {
     e = cudaDeviceGetAttribute(&v, cudaDevAttrMaxSharedMemoryPerBlockOptin, p->device);
     if (e != cudaSuccess) return cuda_fail(e, "cudaDeviceGetAttribute(smem)");
     p->smem_optin = size_t(v);
+    e = cudaMalloc(&p->d_shifts, p->shifts.size() * sizeof(int32_t));
+    if (e != cudaSuccess) return cuda_fail(e, "cudaMalloc(shifts)");
+    e = cudaMemcpy(p->d_shifts, p->shifts.data(), p->shifts.size() * sizeof(int32_t),
+                   cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaMemcpy(shifts)");
     e = cudaMalloc(&p->d_err, sizeof(int));
     if (e != cudaSuccess) return cuda_fail(e, "cudaMalloc(err)");
     e = cudaMemset(p->d_err, 0, sizeof(int));
@@ -260,6 +391,7 @@ void dd_plan_destroy(dd_plan p) {
     free_fwd_tables(&p->fwd);
     free_adj_tables(&p->adj);
     if (p->d_err) cudaFree(p->d_err);
+    if (p->d_shifts) cudaFree(p->d_shifts);
     if (p->h_in_dev) cudaFree(p->h_in_dev);
     if (p->h_w_dev) cudaFree(p->h_w_dev);
     if (p->h_out_dev) cudaFree(p->h_out_dev);
@@ -295,24 +427,29 @@ dd_status dd_plan_set_variant(dd_plan p, const dd_variant *v) {
     return DD_OK;
 }
 
+// The variant grid: every compiled (kind, dm_per_thread, samples_per_thread)
+// key with every CTA shape, then chunk size and staging depth innermost.
+namespace {
+const int kShapes[6][2] = {{4, 2}, {2, 4}, {8, 1}, {1, 8}, {4, 1}, {2, 2}};
+const int kCch[3] = {8, 16, 4};
+const int kStages[3] = {3, 2, 4};
+}  // namespace
+
 int32_t dd_variant_count(void) {
-    static const int wshapes = 7, cchs = 3, stages = 3;
-    return int32_t(fwd_compiled_keys().size()) * wshapes * cchs * stages;
+    return int32_t(fwd_compiled_keys().size()) * 6 * 3 * 3;
 }
 
 dd_status dd_variant_get(int32_t i, dd_variant *v) {
-    static const int W[7][2] = {{4, 2}, {2, 4}, {8, 1}, {1, 8}, {4, 1}, {2, 2}, {1, 4}};
-    static const int CCH[3] = {8, 4, 16};
     if (!v || i < 0 || i >= dd_variant_count()) return fail(DD_ERR_ARG, "variant index");
     const auto &keys = fwd_compiled_keys();
     const int st = i % 3;
     i /= 3;
     const int cc = i % 3;
     i /= 3;
-    const int ws = i % 7;
-    i /= 7;
+    const int ws = i % 6;
+    i /= 6;
     const FwdKernelKey k = keys[size_t(i)];
-    *v = dd_variant{k.dpt, k.spt, W[ws][0], W[ws][1], CCH[cc], 2 + st};
+    *v = dd_variant{k.kind, k.dpt, k.spt, kShapes[ws][0], kShapes[ws][1], kCch[cc], kStages[st]};
     return DD_OK;
 }
 
