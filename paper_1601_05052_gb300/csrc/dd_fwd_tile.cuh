@@ -5,38 +5,34 @@
 // A tile is (beam b, DM tile of Dt trials, time tile of Ts output samples)
 // and computes out[b][d][t] = sum_c w[c] * in[b][c][t + shift[d][c]] for its
 // trials and samples (Algorithm 1, Section III-A, with weights; the 2-D
-// work-group decomposition of Section III-B). Each warp owns DPT trials by
-// 32*SPT samples; a thread accumulates DPT x SPT outputs in registers.
+// work-group decomposition of Section III-B). Each trial warp owns DPT
+// trials by 32*SPT samples; a thread accumulates DPT x SPT outputs in
+// registers.
 //
-// Staging (Section III-B's shared "local memory"): for each chunk of
-// channels one elected thread copies, per channel, the union of the tile's
-// shifted input windows with one 1-D TMA bulk copy into a pipeline slot,
-// together with the chunk's table of per-trial smem offsets. Slots are
-// recycled through two mbarriers each: `full` (TMA transaction bytes) and
-// `empty` (one arrival per warp once it has read the slot), so warps never
-// wait for each other at a CTA-wide barrier.
+// Staging (Section III-B's shared "local memory"): channels are taken in
+// chunks. For each chunk one warp copies, per channel (one lane each), the
+// union of the tile's shifted input windows with a 1-D TMA bulk copy into a
+// pipeline slot, together with the chunk's tables and weights; the slot's
+// `full` mbarrier counts the bytes. Channel descriptors are read one chunk
+// ahead so the copies go out without waiting on global memory.
 //
-// Two ways to turn a staged window into sums (the `kind` of a variant):
+// Ways to turn a staged window into sums (the `kind` of a variant):
 //  kind 0, lane-strided: lane l owns samples l, l+32, ...; every add reads
 //    its operand from shared memory (conflict-free, one word per add).
-//  kind 1, register window: a thread owns SPT consecutive samples (SPT odd
-//    so that a warp's loads hit 32 distinct banks). Per channel it loads the
-//    union window of its warp's DPT trials, SPT + span words, into registers
-//    once and serves all DPT trials from it: the trial's delay relative to
-//    the group's smallest one is warp-uniform and selects, through a switch
-//    over 0..RMAX, a fully unrolled block with compile-time register indices.
-//    That cuts shared-memory reads per add from 1 to (SPT+span)/(DPT*SPT).
-//    Channels whose group span exceeds RMAX take the kind-0 style path.
+//    Slots are recycled through `empty` mbarriers (one arrival per warp).
+//  kind 1, register window: a thread owns SPT (odd) consecutive samples;
+//    per channel it loads its warp's union window into registers once and
+//    serves every trial from it through a warp-uniform switch on the
+//    trial's relative delay (0..15); wider groups take a direct path.
 //  kind 2, sub-band partial sums: channels form groups of 4; inside a DM
-//    tile the trials of a group share only a few distinct relative delay
-//    patterns, so after a chunk lands the CTA builds each pattern's weighted
-//    4-channel partial series in shared memory once, and the lane-strided
-//    trial loop then adds one partial value per group instead of one input
-//    value per channel (the same sums, associated per group).
-//  kind 3, warp-specialised sub-band: kind 2's arithmetic, but 4 extra
-//    builder warps turn staged windows into partial series while the trial
-//    warps consume earlier ones; full/empty mbarriers on the staging slots
-//    and on 3 partial-sum slots replace every CTA-wide barrier.
+//    tile the trials of a group share few distinct relative delay patterns,
+//    so the CTA builds each pattern's weighted 4-channel partial series in
+//    shared memory once per chunk and the lane-strided trial loop adds one
+//    partial value per group instead of one input value per channel (the
+//    same sums, associated per group). One CTA barrier per chunk.
+//  kind 3, warp-specialised sub-band: kind 2's arithmetic with 4 extra
+//    builder warps; mbarriers on the staging slots and on 3 partial-sum
+//    slots replace every CTA-wide barrier.
 #pragma once
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
@@ -47,14 +43,20 @@
 #include "dd_ptx.cuh"
 
 // The compiled forward kernels: X(kind, dm_per_thread, samples_per_thread).
-#define DD_FWD_KEYS(X)                                                                   \
-    X(0, 2, 4) X(0, 4, 2) X(0, 4, 4) X(0, 8, 2) X(0, 8, 4) X(0, 4, 8) X(1, 8, 9) X(1, 4, 15) \
-        X(2, 4, 4) X(2, 4, 8) X(2, 8, 4) X(2, 8, 2) X(3, 8, 4) X(3, 4, 8) X(3, 8, 2)
+#define DD_FWD_KEYS(X)                                                                    \
+    X(0, 2, 4) X(0, 4, 2) X(0, 4, 4) X(0, 8, 2) X(0, 8, 4) X(0, 4, 8) X(1, 8, 9) X(2, 4, 4) \
+        X(2, 4, 8) X(2, 8, 4) X(2, 8, 2) X(3, 8, 4) X(3, 4, 8) X(3, 8, 2)
 
 namespace dd {
 
 // Largest relative delay inside a warp's trial group served from registers.
 constexpr int kRwRmax = 15;
+// Channels per group and patterns per group of the sub-band kinds; builder
+// warps and partial-sum slots of kind 3.
+constexpr int kSbG = 4;
+constexpr int kSbP = 8;
+constexpr int kWsBuilders = 4;
+constexpr int kWsPSlots = 3;
 
 template <typename T>
 struct Elem;
@@ -95,17 +97,10 @@ struct FwdArgs {
     int n_dtiles, n_ttiles, B;
     const int4 *desc;
     const uint16_t *offs;
-    const int4 *bdesc;  // kind 2 only
-    int p_elems;        // kind 2 only
+    const int4 *bdesc;  // kinds 2 and 3
+    int p_elems;        // kinds 2 and 3
     int *err;
 };
-
-// Channels per group and patterns per group of the sub-band kinds; builder
-// warps and partial-sum slots of kind 3.
-constexpr int kSbG = 4;
-constexpr int kSbP = 8;
-constexpr int kWsBuilders = 4;
-constexpr int kWsPSlots = 3;
 
 // Loads the DPT uint16 smem offsets of this warp's trials with one vector
 // load (4/8/16-byte aligned by construction of the tables).
@@ -133,12 +128,118 @@ __device__ __forceinline__ void load_offsets(const uint16_t *p, int (&o)[DPT]) {
     }
 }
 
+// ------------------------------------------------------------------ staging
+
+// Per-tile staging context. Layout of a slot: [window data: stage_data_bytes]
+// [tables: tab_bytes][weights: 16-byte rounded cch words].
+template <typename T>
+struct Stager {
+    const FwdArgs &a;
+    const T *in_b;
+    long long t0;
+    const int4 *desc_k;
+    const void *tab_k;    // kind 0/1: trial offsets; kind 2/3: group offsets
+    const int4 *bdesc_k;  // kind 2/3 only
+    uint32_t tab_bytes;   // per chunk, both tables
+    uint32_t tab1_bytes;  // per chunk, first table
+    unsigned char *stage0;
+    int stage_bytes;
+    bool subband;
+
+    // Descriptor of this lane's channel in chunk k (zero beyond the chunk).
+    __device__ __forceinline__ int4 desc(int k, int lane) const {
+        const int c = k * a.cch + lane;
+        return (lane < a.cch && c < a.C) ? desc_k[c] : make_int4(0, 0, 0, 0);
+    }
+
+    // Warp-cooperative: stage chunk k into `slot`, each lane < channels
+    // copying its channel's window (descriptor `dsc` preloaded), lane 0 the
+    // tables and weights. All 32 lanes of one warp must call it.
+    __device__ __forceinline__ void issue(int k, int slot, int4 dsc, uint64_t *full,
+                                          int lane) const {
+        unsigned char *sb = stage0 + slot * stage_bytes;
+        const int c0 = k * a.cch;
+        const int nch = min(a.cch, a.C - c0);
+        const long long g0 = t0 + dsc.x;
+        uint32_t bytes = 0;
+        if (lane < nch)
+            bytes = uint32_t(min((long long)dsc.y, a.stride - g0)) * uint32_t(sizeof(T));
+        uint32_t total = bytes;
+#pragma unroll
+        for (int m = 16; m >= 1; m >>= 1) total += __shfl_xor_sync(0xffffffffu, total, m);
+        const uint32_t w_bytes = uint32_t((nch * 4 + 15) & ~15);
+        if (lane == 0) mbar_arrive_expect_tx(full, total + tab_bytes + w_bytes);
+        __syncwarp();
+        fence_proxy_async_smem();
+        if (bytes)
+            bulk_g2s(sb + (size_t)dsc.z * sizeof(T), in_b + (long long)(c0 + lane) * a.stride + g0,
+                     bytes, full);
+        if (lane == 0) {
+            unsigned char *tb = sb + a.stage_data_bytes;
+            if (!subband) {
+                bulk_g2s(tb, static_cast<const uint16_t *>(tab_k) + (size_t)c0 * a.Dt, tab_bytes,
+                         full);
+            } else {
+                const int g0i = c0 / kSbG;
+                bulk_g2s(tb, static_cast<const uint16_t *>(tab_k) + (size_t)g0i * a.Dt,
+                         tab1_bytes, full);
+                bulk_g2s(tb + tab1_bytes, bdesc_k + (size_t)g0i * kSbP * 2, tab_bytes - tab1_bytes,
+                         full);
+            }
+            // the chunk's weights; a 16-byte granule never crosses a page, so
+            // rounding the last chunk up stays inside the weight buffer's page
+            bulk_g2s(tb + tab_bytes, static_cast<const uint32_t *>(a.w) + c0, w_bytes, full);
+        }
+    }
+};
+
+template <typename T>
+__device__ __forceinline__ Stager<T> make_stager(const FwdArgs &a, int dtile, int b, long long t0,
+                                                 unsigned char *stage0, bool subband) {
+    const int gpc = a.cch / kSbG;
+    const int g_pad = a.C_pad / kSbG;
+    Stager<T> s{a,
+                static_cast<const T *>(a.in) + (long long)b * a.C * a.stride,
+                t0,
+                a.desc + (size_t)dtile * a.C_pad,
+                subband ? static_cast<const void *>(a.offs + (size_t)dtile * g_pad * a.Dt)
+                        : static_cast<const void *>(a.offs + (size_t)dtile * a.C_pad * a.Dt),
+                subband ? a.bdesc + (size_t)dtile * g_pad * kSbP * 2 : nullptr,
+                subband ? uint32_t(gpc) * a.Dt * 2 + uint32_t(gpc) * kSbP * 32
+                        : uint32_t(a.cch) * a.Dt * 2,
+                subband ? uint32_t(gpc) * a.Dt * 2 : uint32_t(a.cch) * a.Dt * 2,
+                stage0,
+                a.stage_data_bytes + a.stage_offs_bytes,
+                subband};
+    return s;
+}
+
+// Stores a thread's accumulators (lane-strided sample mapping).
+template <typename Acc, int DPT, int SPT>
+__device__ __forceinline__ void store_lane_strided(const FwdArgs &a, const Acc (&acc)[DPT][SPT],
+                                                   int dtile, int b, long long t0, int wd, int lb) {
+    Acc *out = static_cast<Acc *>(a.out);
+#pragma unroll
+    for (int i = 0; i < DPT; ++i) {
+        const int d = dtile * a.Dt + wd * DPT + i;
+        if (d >= a.D) continue;
+        Acc *orow = out + ((long long)b * a.D + d) * a.S + t0 + lb;
+        const long long tmax = a.S - t0 - lb;
+#pragma unroll
+        for (int j = 0; j < SPT; ++j)
+            if (32 * j < tmax) orow[32 * j] = acc[i][j];
+    }
+}
+
+// ------------------------------------------------------------------ kinds 0 and 1
+
 // kind 0: lane-strided samples, one shared-memory read per add.
 template <typename T, int DPT, int SPT>
 struct LaneStrided {
     using Acc = typename Elem<T>::Acc;
     using Wt = typename Elem<T>::W;
-    __device__ static int sample_of(int lane, int j) { return lane + 32 * j; }
+    __device__ static int sample_of(int j) { return 32 * j; }
+    __device__ static int lane_base(int wt, int lane) { return wt * 32 * SPT + lane; }
     __device__ static void channel(Acc (&acc)[DPT][SPT], const T *sdata, int lane_base,
                                    const int (&o)[DPT], Wt wc) {
         const T *s = sdata + lane_base;
@@ -149,7 +250,6 @@ struct LaneStrided {
             for (int j = 0; j < SPT; ++j) acc[i][j] += wc * Elem<T>::val(src[32 * j]);
         }
     }
-    __device__ static int lane_base(int wt, int lane) { return wt * 32 * SPT + lane; }
 };
 
 // kind 1: thread-contiguous samples served from a register window.
@@ -159,7 +259,7 @@ struct RegWindow {
     using Wt = typename Elem<T>::W;
     static_assert(SPT % 2 == 1, "odd samples_per_thread keeps window loads conflict-free");
     static constexpr int R = kRwRmax;
-    __device__ static int sample_of(int lane, int j) { return lane * SPT + j; }
+    __device__ static int sample_of(int j) { return j; }
     __device__ static int lane_base(int wt, int lane) { return wt * 32 * SPT + lane * SPT; }
 
     template <int RR>
@@ -184,7 +284,8 @@ struct RegWindow {
 #pragma unroll
             for (int k = 0; k < SPT; ++k) win[k] = Elem<T>::val(src[k]);
 #pragma unroll
-            for (int k = SPT; k < SPT + R; ++k) win[k] = (k < SPT + span) ? Elem<T>::val(src[k]) : Acc(0);
+            for (int k = SPT; k < SPT + R; ++k)
+                win[k] = (k < SPT + span) ? Elem<T>::val(src[k]) : Acc(0);
 #pragma unroll
             for (int i = 0; i < DPT; ++i) {
                 switch (o[i] - gb) {
@@ -208,23 +309,18 @@ struct RegWindow {
     }
 };
 
-template <int KIND, typename T, int DPT, int SPT>
-using FwdPolicy = typename std::conditional<KIND == 1, RegWindow<T, DPT, SPT>,
-                                            LaneStrided<T, DPT, SPT>>::type;
-
-// Shared-memory layout of a forward CTA: `full` mbarriers at byte 0, `empty`
-// mbarriers at byte 64 (stages <= 4), then `stages` slots of (data, offsets)
-// from byte 128.
-// kind 3 uses bars[4..6] / bars[12..14] for its partial-sum slots and counts
-// builder warps on the staging slots' empty barriers.
+// Barriers: kinds 0-2 use full[s] = bars[s] (producer arrival + bytes) and,
+// for kinds 0/1, empty[s] = bars[8 + s] (one arrival per warp). Kind 3 uses
+// bars[4..6] / bars[12..14] for its partial-sum slots and counts builder
+// warps on the staging slots' empty barriers.
 template <int KIND>
 __device__ __forceinline__ void fwd_init_barriers(uint64_t *bars, int stages) {
     if (threadIdx.x == 0) {
         const int n_warps = int(blockDim.x >> 5);
-        const int builders = KIND == 3 ? kWsBuilders : n_warps;
+        const int releasers = KIND == 3 ? kWsBuilders : n_warps;
         for (int s = 0; s < stages; ++s) {
             mbar_init(&bars[s], 1);
-            mbar_init(&bars[8 + s], uint32_t(builders));
+            mbar_init(&bars[8 + s], uint32_t(releasers));
         }
         if (KIND == 3) {
             for (int q = 0; q < kWsPSlots; ++q) {
@@ -237,7 +333,7 @@ __device__ __forceinline__ void fwd_init_barriers(uint64_t *bars, int stages) {
     __syncthreads();
 }
 
-// Computes one tile. `kbase` counts the chunks this CTA has already pushed
+// Kinds 0 and 1. `kbase` counts the chunks this CTA has already pushed
 // through its slots; chunk kg uses slot kg % stages, and the n-th completion
 // of a slot's full/empty barrier belongs to chunk slot + n * stages, so the
 // phase parities carry over from tile to tile without re-initialisation.
@@ -245,52 +341,29 @@ template <int KIND, typename T, int DPT, int SPT>
 __device__ __forceinline__ void fwd_tile(const FwdArgs &a, int dtile, int ttile, int b,
                                          uint64_t *bars, unsigned char *stage0,
                                          uint32_t &kbase) {
-    using P = FwdPolicy<KIND, T, DPT, SPT>;
+    using P = typename std::conditional<KIND == 1, RegWindow<T, DPT, SPT>,
+                                        LaneStrided<T, DPT, SPT>>::type;
     using Acc = typename Elem<T>::Acc;
     using Wt = typename Elem<T>::W;
     uint64_t *full = bars;
     uint64_t *empty = bars + 8;
     const uint32_t S = uint32_t(a.stages);
-    const int stage_bytes = a.stage_data_bytes + a.stage_offs_bytes;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int wd = warp % a.warps_dm, wt = warp / a.warps_dm;
     const long long t0 = (long long)ttile * a.Ts;
-    const T *in_b = static_cast<const T *>(a.in) + (long long)b * a.C * a.stride;
-    const Wt *w = static_cast<const Wt *>(a.w);
     const int n_chunks = (a.C + a.cch - 1) / a.cch;
-    const int4 *desc_k = a.desc + (size_t)dtile * a.C_pad;
-    const uint16_t *offs_k = a.offs + (size_t)dtile * a.C_pad * a.Dt;
-    const uint32_t offs_bytes = uint32_t(a.cch) * a.Dt * 2;
+    const Stager<T> st = make_stager<T>(a, dtile, b, t0, stage0, false);
 
-    // Elected thread: stage tile chunk k (global chunk kbase + k).
-    auto issue = [&](int k) {
+    // warp 0 stages chunk k, after the slot's previous chunk was released
+    auto issue = [&](int k, int4 dsc) {
         const uint32_t kg = kbase + uint32_t(k);
         const int slot = int(kg % S);
         if (kg >= S) mbar_wait_bounded(&empty[slot], ((kg / S) - 1u) & 1u, a.err);
-        fence_proxy_async_smem();
-        unsigned char *sb = stage0 + slot * stage_bytes;
-        const int c0 = k * a.cch;
-        const int nch = min(a.cch, a.C - c0);
-        uint32_t total = offs_bytes;
-        for (int cc = 0; cc < nch; ++cc) {
-            const int4 dsc = desc_k[c0 + cc];
-            const long long n = min((long long)dsc.y, a.stride - (t0 + dsc.x));
-            total += uint32_t(n) * uint32_t(sizeof(T));
-        }
-        mbar_arrive_expect_tx(&full[slot], total);
-        for (int cc = 0; cc < nch; ++cc) {
-            const int4 dsc = desc_k[c0 + cc];
-            const long long g0 = t0 + dsc.x;
-            const long long n = min((long long)dsc.y, a.stride - g0);
-            bulk_g2s(sb + (size_t)dsc.z * sizeof(T), in_b + (long long)(c0 + cc) * a.stride + g0,
-                     uint32_t(n) * uint32_t(sizeof(T)), &full[slot]);
-        }
-        bulk_g2s(sb + a.stage_data_bytes, offs_k + (size_t)c0 * a.Dt, offs_bytes, &full[slot]);
+        st.issue(k, slot, dsc, &full[slot], lane);
     };
-
-    if (tid == 0) {
+    if (warp == 0) {
         const int pro = min(int(S), n_chunks);
-        for (int k = 0; k < pro; ++k) issue(k);
+        for (int k = 0; k < pro; ++k) issue(k, st.desc(k, lane));
     }
 
     Acc acc[DPT][SPT];
@@ -303,26 +376,27 @@ __device__ __forceinline__ void fwd_tile(const FwdArgs &a, int dtile, int ttile,
     for (int k = 0; k < n_chunks; ++k) {
         const uint32_t kg = kbase + uint32_t(k);
         const int slot = int(kg % S);
+        const int kn = k - 1 + int(S);  // the chunk warp 0 stages after this one
+        int4 pre = make_int4(0, 0, 0, 0);
+        if (warp == 0 && k >= 1 && kn < n_chunks) pre = st.desc(kn, lane);
         mbar_wait_bounded(&full[slot], (kg / S) & 1u, a.err);
-        const unsigned char *sb = stage0 + slot * stage_bytes;
+        const unsigned char *sb = stage0 + slot * st.stage_bytes;
         const T *sdata = reinterpret_cast<const T *>(sb);
         const uint16_t *soffs =
             reinterpret_cast<const uint16_t *>(sb + a.stage_data_bytes) + wd * DPT;
-        const int c0 = k * a.cch;
-        const int nch = min(a.cch, a.C - c0);
+        const Wt *sw = reinterpret_cast<const Wt *>(sb + a.stage_data_bytes + st.tab_bytes);
+        const int nch = min(a.cch, a.C - k * a.cch);
         for (int cc = 0; cc < nch; ++cc) {
-            const Wt wc = __ldg(w + c0 + cc);
             int o[DPT];
             load_offsets<DPT>(soffs + cc * a.Dt, o);
-            P::channel(acc, sdata, lb, o, wc);
+            P::channel(acc, sdata, lb, o, sw[cc]);
         }
         __syncwarp();
         if (lane == 0) mbar_arrive(&empty[slot]);
         // refill the slot of the previous chunk (one chunk of slack for the
         // other warps), keeping stages-1 chunks in flight
-        if (tid == 0 && k >= 1 && k - 1 + int(S) < n_chunks) issue(k - 1 + int(S));
+        if (warp == 0 && k >= 1 && kn < n_chunks) issue(kn, pre);
     }
-    // the last chunk's slot: refills for k-1+S < n_chunks were all issued above
     kbase += uint32_t(n_chunks);
 
     Acc *out = static_cast<Acc *>(a.out);
@@ -330,16 +404,17 @@ __device__ __forceinline__ void fwd_tile(const FwdArgs &a, int dtile, int ttile,
     for (int i = 0; i < DPT; ++i) {
         const int d = dtile * a.Dt + wd * DPT + i;
         if (d >= a.D) continue;
-        Acc *orow = out + ((long long)b * a.D + d) * a.S + t0 + (lb - 0);
+        Acc *orow = out + ((long long)b * a.D + d) * a.S + t0 + lb;
         const long long tmax = a.S - t0 - lb;
 #pragma unroll
         for (int j = 0; j < SPT; ++j) {
-            const int off = P::sample_of(0, j);
+            const int off = P::sample_of(j);
             if (off < tmax) orow[off] = acc[i][j];
         }
     }
 }
 
+// ------------------------------------------------------------------ kinds 2 and 3
 
 // Builds one partial series: dst[u] = sum_{j<gn} wg[j] * raw[r[j] + u] for
 // u < L, lanes of a warp striding by 32 and each lane keeping 4 elements in
@@ -377,10 +452,50 @@ __device__ __forceinline__ void sb_build(typename Elem<T>::Acc *dst, const T *ra
     }
 }
 
-// kind 2: sub-band partial sums (see the file comment). One CTA barrier per
-// chunk separates the build of the chunk's partial series from the trial
-// loop; the partial-sum buffer alternates between two halves by global chunk
-// parity so a chunk's build never overwrites what slower warps still read.
+// Builds the partial series of build entries e = first, first + step, ... of
+// one chunk (entry = group * kSbP + pattern).
+template <typename T>
+__device__ __forceinline__ void sb_build_entries(typename Elem<T>::Acc *P, const T *raw,
+                                                 const int4 *bd, const typename Elem<T>::W *sw,
+                                                 int ng, int first, int step, int lane) {
+    using Wt = typename Elem<T>::W;
+    for (int e = first; e < ng * kSbP; e += step) {
+        const int4 A = bd[2 * e];
+        if (A.y == 0) continue;
+        const int4 B = bd[2 * e + 1];
+        const int g = e / kSbP;
+        const int gn = B.z;
+        Wt wg[4];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) wg[j] = j < gn ? sw[g * kSbG + j] : Wt(0);
+        const int r[4] = {A.z, A.w, B.x, B.y};
+        sb_build<T>(P + A.x, raw, r, wg, gn, A.y, lane);
+    }
+}
+
+// The trial loop of a sub-band chunk: one partial value per group per output.
+template <typename Acc, int DPT, int SPT>
+__device__ __forceinline__ void sb_trials(Acc (&acc)[DPT][SPT], const Acc *Pl,
+                                          const uint16_t *poffs, int Dt, int ng) {
+#pragma unroll
+    for (int g = 0; g < 4; ++g) {  // at most 16 channels = 4 groups per chunk
+        if (g < ng) {
+            int o[DPT];
+            load_offsets<DPT>(poffs + g * Dt, o);
+#pragma unroll
+            for (int i = 0; i < DPT; ++i) {
+                const Acc *src = Pl + o[i];
+#pragma unroll
+                for (int j = 0; j < SPT; ++j) acc[i][j] += src[32 * j];
+            }
+        }
+    }
+}
+
+// kind 2: sub-band partial sums. One CTA barrier per chunk separates the
+// build of the chunk's partial series from the trial loop; the partial-sum
+// buffer alternates between two halves by global chunk parity so a chunk's
+// build never overwrites what slower warps still read.
 template <typename T, int DPT, int SPT>
 __device__ __forceinline__ void fwd_tile_sb(const FwdArgs &a, int dtile, int ttile, int b,
                                             uint64_t *bars, unsigned char *stage0,
@@ -389,53 +504,19 @@ __device__ __forceinline__ void fwd_tile_sb(const FwdArgs &a, int dtile, int tti
     using Wt = typename Elem<T>::W;
     uint64_t *full = bars;
     const uint32_t S = uint32_t(a.stages);
-    const int stage_bytes = a.stage_data_bytes + a.stage_offs_bytes;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int n_warps = int(blockDim.x >> 5);
     const int wd = warp % a.warps_dm, wt = warp / a.warps_dm;
     const long long t0 = (long long)ttile * a.Ts;
-    const T *in_b = static_cast<const T *>(a.in) + (long long)b * a.C * a.stride;
-    const Wt *w = static_cast<const Wt *>(a.w);
     const int n_chunks = (a.C + a.cch - 1) / a.cch;
-    const int gpc = a.cch / kSbG;
-    const int g_pad = a.C_pad / kSbG;
-    const int4 *desc_k = a.desc + (size_t)dtile * a.C_pad;
-    const uint16_t *offs_k = a.offs + (size_t)dtile * g_pad * a.Dt;
-    const int4 *bdesc_k = a.bdesc + (size_t)dtile * g_pad * kSbP * 2;
-    const uint32_t poffs_bytes = uint32_t(gpc) * a.Dt * 2;
-    const uint32_t bdesc_bytes = uint32_t(gpc) * kSbP * 32;
-    Acc *pbuf = reinterpret_cast<Acc *>(stage0 + S * stage_bytes);
+    const Stager<T> st = make_stager<T>(a, dtile, b, t0, stage0, true);
+    Acc *pbuf = reinterpret_cast<Acc *>(stage0 + S * st.stage_bytes);
+    auto slot_of = [&](int k) { return int((kbase + uint32_t(k)) % S); };
 
-    auto issue = [&](int k) {
-        const uint32_t kg = kbase + uint32_t(k);
-        const int slot = int(kg % S);
-        fence_proxy_async_smem();
-        unsigned char *sb = stage0 + slot * stage_bytes;
-        const int c0 = k * a.cch;
-        const int nch = min(a.cch, a.C - c0);
-        uint32_t total = poffs_bytes + bdesc_bytes;
-        for (int cc = 0; cc < nch; ++cc) {
-            const int4 dsc = desc_k[c0 + cc];
-            const long long n = min((long long)dsc.y, a.stride - (t0 + dsc.x));
-            total += uint32_t(n) * uint32_t(sizeof(T));
-        }
-        mbar_arrive_expect_tx(&full[slot], total);
-        for (int cc = 0; cc < nch; ++cc) {
-            const int4 dsc = desc_k[c0 + cc];
-            const long long g0 = t0 + dsc.x;
-            const long long n = min((long long)dsc.y, a.stride - g0);
-            bulk_g2s(sb + (size_t)dsc.z * sizeof(T), in_b + (long long)(c0 + cc) * a.stride + g0,
-                     uint32_t(n) * uint32_t(sizeof(T)), &full[slot]);
-        }
-        const int g0i = c0 / kSbG;
-        bulk_g2s(sb + a.stage_data_bytes, offs_k + (size_t)g0i * a.Dt, poffs_bytes, &full[slot]);
-        bulk_g2s(sb + a.stage_data_bytes + poffs_bytes, bdesc_k + (size_t)g0i * kSbP * 2,
-                 bdesc_bytes, &full[slot]);
-    };
-
-    if (tid == 0) {
+    if (warp == 0) {
         const int pro = min(int(S), n_chunks);
-        for (int k = 0; k < pro; ++k) issue(k);
+        for (int k = 0; k < pro; ++k)
+            st.issue(k, slot_of(k), st.desc(k, lane), &full[slot_of(k)], lane);
     }
 
     Acc acc[DPT][SPT];
@@ -448,59 +529,28 @@ __device__ __forceinline__ void fwd_tile_sb(const FwdArgs &a, int dtile, int tti
     for (int k = 0; k < n_chunks; ++k) {
         const uint32_t kg = kbase + uint32_t(k);
         const int slot = int(kg % S);
+        const int kn = k - 1 + int(S);
+        int4 pre = make_int4(0, 0, 0, 0);
+        if (warp == 0 && k >= 1 && kn < n_chunks) pre = st.desc(kn, lane);
         mbar_wait_bounded(&full[slot], (kg / S) & 1u, a.err);
-        const unsigned char *sb = stage0 + slot * stage_bytes;
+        const unsigned char *sb = stage0 + slot * st.stage_bytes;
         const T *raw = reinterpret_cast<const T *>(sb);
         const uint16_t *poffs = reinterpret_cast<const uint16_t *>(sb + a.stage_data_bytes);
-        const int4 *bd = reinterpret_cast<const int4 *>(sb + a.stage_data_bytes + poffs_bytes);
+        const int4 *bd = reinterpret_cast<const int4 *>(sb + a.stage_data_bytes + st.tab1_bytes);
+        const Wt *sw = reinterpret_cast<const Wt *>(sb + a.stage_data_bytes + st.tab_bytes);
         Acc *P = pbuf + (kg & 1u) * a.p_elems;
-        const int c0 = k * a.cch;
-        const int ng = (min(a.cch, a.C - c0) + kSbG - 1) / kSbG;
+        const int ng = (min(a.cch, a.C - k * a.cch) + kSbG - 1) / kSbG;
 
-        // build every pattern's partial series of this chunk
-        for (int e = warp; e < ng * kSbP; e += n_warps) {
-            const int4 A = bd[2 * e];
-            if (A.y == 0) continue;
-            const int4 B = bd[2 * e + 1];
-            const int g = e / kSbP;
-            const int gn = B.z;
-            const int r[4] = {A.z, A.w, B.x, B.y};
-            Wt wg[4];
-#pragma unroll
-            for (int j = 0; j < 4; ++j) wg[j] = j < gn ? __ldg(w + c0 + g * kSbG + j) : Wt(0);
-            sb_build<T>(P + A.x, raw, r, wg, gn, A.y, lane);
-        }
+        sb_build_entries<T>(P, raw, bd, sw, ng, warp, n_warps, lane);
         __syncthreads();
         // every warp has finished the trial loop of chunk k-1 (it precedes the
-        // build of chunk k), so that chunk's slot, offsets included, is free
-        if (tid == 0 && k >= 1 && k - 1 + int(S) < n_chunks) issue(k - 1 + int(S));
-
-        // trial loop over the chunk's channel groups
-        const Acc *Pl = P + lb;
-        for (int g = 0; g < ng; ++g) {
-            int o[DPT];
-            load_offsets<DPT>(poffs + g * a.Dt + wd * DPT, o);
-#pragma unroll
-            for (int i = 0; i < DPT; ++i) {
-                const Acc *src = Pl + o[i];
-#pragma unroll
-                for (int j = 0; j < SPT; ++j) acc[i][j] += src[32 * j];
-            }
-        }
+        // build of chunk k), so that chunk's slot, tables included, is free
+        if (warp == 0 && k >= 1 && kn < n_chunks)
+            st.issue(kn, slot_of(kn), pre, &full[slot_of(kn)], lane);
+        sb_trials<Acc, DPT, SPT>(acc, P + lb, poffs + wd * DPT, a.Dt, ng);
     }
     kbase += uint32_t(n_chunks);
-
-    Acc *out = static_cast<Acc *>(a.out);
-#pragma unroll
-    for (int i = 0; i < DPT; ++i) {
-        const int d = dtile * a.Dt + wd * DPT + i;
-        if (d >= a.D) continue;
-        Acc *orow = out + ((long long)b * a.D + d) * a.S + t0 + lb;
-        const long long tmax = a.S - t0 - lb;
-#pragma unroll
-        for (int j = 0; j < SPT; ++j)
-            if (32 * j < tmax) orow[32 * j] = acc[i][j];
-    }
+    store_lane_strided<Acc, DPT, SPT>(a, acc, dtile, b, t0, wd, lb);
 }
 
 // kind 3: warp-specialised sub-band. Warps [0, NC) are trial warps (as in
@@ -517,84 +567,45 @@ __device__ __forceinline__ void fwd_tile_ws(const FwdArgs &a, int dtile, int tti
     using Wt = typename Elem<T>::W;
     uint64_t *full_r = bars, *empty_r = bars + 8, *full_p = bars + 4, *empty_p = bars + 12;
     const uint32_t S = uint32_t(a.stages), Q = uint32_t(kWsPSlots);
-    const int stage_bytes = a.stage_data_bytes + a.stage_offs_bytes;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int nc = int(blockDim.x >> 5) - kWsBuilders;  // trial warps
     const long long t0 = (long long)ttile * a.Ts;
     const int n_chunks = (a.C + a.cch - 1) / a.cch;
-    const int gpc = a.cch / kSbG;
-    const uint32_t poffs_bytes = uint32_t(gpc) * a.Dt * 2;
+    const Stager<T> st = make_stager<T>(a, dtile, b, t0, stage0, true);
+    const uint32_t poffs_bytes = st.tab1_bytes;
     const int pslot_bytes = a.p_elems * int(sizeof(Acc)) + int(poffs_bytes);
-    unsigned char *pslot0 = stage0 + S * stage_bytes;
+    unsigned char *pslot0 = stage0 + S * st.stage_bytes;
 
     if (warp >= nc) {
         // ---------------- builder warps
         const int bw = warp - nc;
-        const T *in_b = static_cast<const T *>(a.in) + (long long)b * a.C * a.stride;
-        const Wt *w = static_cast<const Wt *>(a.w);
-        const int g_pad = a.C_pad / kSbG;
-        const int4 *desc_k = a.desc + (size_t)dtile * a.C_pad;
-        const uint16_t *offs_k = a.offs + (size_t)dtile * g_pad * a.Dt;
-        const int4 *bdesc_k = a.bdesc + (size_t)dtile * g_pad * kSbP * 2;
-        const uint32_t bdesc_bytes = uint32_t(gpc) * kSbP * 32;
-        auto issue = [&](int k) {  // one lane of builder warp 0
+        auto issue = [&](int k, int4 dsc) {  // builder warp 0
             const uint32_t kg = kbase + uint32_t(k);
             const int slot = int(kg % S);
             if (kg >= S) mbar_wait_bounded(&empty_r[slot], ((kg / S) - 1u) & 1u, a.err);
-            fence_proxy_async_smem();
-            unsigned char *sb = stage0 + slot * stage_bytes;
-            const int c0 = k * a.cch;
-            const int nch = min(a.cch, a.C - c0);
-            uint32_t total = poffs_bytes + bdesc_bytes;
-            for (int cc = 0; cc < nch; ++cc) {
-                const int4 dsc = desc_k[c0 + cc];
-                const long long n = min((long long)dsc.y, a.stride - (t0 + dsc.x));
-                total += uint32_t(n) * uint32_t(sizeof(T));
-            }
-            mbar_arrive_expect_tx(&full_r[slot], total);
-            for (int cc = 0; cc < nch; ++cc) {
-                const int4 dsc = desc_k[c0 + cc];
-                const long long g0 = t0 + dsc.x;
-                const long long n = min((long long)dsc.y, a.stride - g0);
-                bulk_g2s(sb + (size_t)dsc.z * sizeof(T),
-                         in_b + (long long)(c0 + cc) * a.stride + g0,
-                         uint32_t(n) * uint32_t(sizeof(T)), &full_r[slot]);
-            }
-            const int g0i = c0 / kSbG;
-            bulk_g2s(sb + a.stage_data_bytes, offs_k + (size_t)g0i * a.Dt, poffs_bytes,
-                     &full_r[slot]);
-            bulk_g2s(sb + a.stage_data_bytes + poffs_bytes, bdesc_k + (size_t)g0i * kSbP * 2,
-                     bdesc_bytes, &full_r[slot]);
+            st.issue(k, slot, dsc, &full_r[slot], lane);
         };
-        if (bw == 0 && lane == 0) {
+        if (bw == 0) {
             const int pro = min(int(S), n_chunks);
-            for (int k = 0; k < pro; ++k) issue(k);
+            for (int k = 0; k < pro; ++k) issue(k, st.desc(k, lane));
         }
-        __syncwarp();
         for (int k = 0; k < n_chunks; ++k) {
             const uint32_t kg = kbase + uint32_t(k);
             const int rs = int(kg % S), ps = int(kg % Q);
+            const int kn = k - 1 + int(S);
+            int4 pre = make_int4(0, 0, 0, 0);
+            if (bw == 0 && k >= 1 && kn < n_chunks) pre = st.desc(kn, lane);
             mbar_wait_bounded(&full_r[rs], (kg / S) & 1u, a.err);
             if (kg >= Q) mbar_wait_bounded(&empty_p[ps], ((kg / Q) - 1u) & 1u, a.err);
-            const unsigned char *sb = stage0 + rs * stage_bytes;
+            const unsigned char *sb = stage0 + rs * st.stage_bytes;
             const T *raw = reinterpret_cast<const T *>(sb);
-            const int4 *bd = reinterpret_cast<const int4 *>(sb + a.stage_data_bytes + poffs_bytes);
+            const int4 *bd =
+                reinterpret_cast<const int4 *>(sb + a.stage_data_bytes + poffs_bytes);
+            const Wt *sw = reinterpret_cast<const Wt *>(sb + a.stage_data_bytes + st.tab_bytes);
             unsigned char *pb = pslot0 + ps * pslot_bytes;
-            Acc *P = reinterpret_cast<Acc *>(pb);
-            const int c0 = k * a.cch;
-            const int ng = (min(a.cch, a.C - c0) + kSbG - 1) / kSbG;
-            for (int e = bw; e < ng * kSbP; e += kWsBuilders) {
-                const int4 A = bd[2 * e];
-                if (A.y == 0) continue;
-                const int4 B = bd[2 * e + 1];
-                const int g = e / kSbP;
-                const int gn = B.z;
-                Wt wg[4];
-#pragma unroll
-                for (int j = 0; j < 4; ++j) wg[j] = j < gn ? __ldg(w + c0 + g * kSbG + j) : Wt(0);
-                const int r[4] = {A.z, A.w, B.x, B.y};
-                sb_build<T>(P + A.x, raw, r, wg, gn, A.y, lane);
-            }
+            const int ng = (min(a.cch, a.C - k * a.cch) + kSbG - 1) / kSbG;
+            sb_build_entries<T>(reinterpret_cast<Acc *>(pb), raw, bd, sw, ng, bw, kWsBuilders,
+                                lane);
             if (bw == 0) {  // the trial offsets travel with the partial sums
                 const uint32_t *src = reinterpret_cast<const uint32_t *>(sb + a.stage_data_bytes);
                 uint32_t *dsto = reinterpret_cast<uint32_t *>(pb + a.p_elems * int(sizeof(Acc)));
@@ -606,8 +617,7 @@ __device__ __forceinline__ void fwd_tile_ws(const FwdArgs &a, int dtile, int tti
                 mbar_arrive(&empty_r[rs]);
             }
             // refill the staging slot of the previous chunk (one chunk of slack)
-            if (bw == 0 && lane == 0 && k >= 1 && k - 1 + int(S) < n_chunks) issue(k - 1 + int(S));
-            __syncwarp();
+            if (bw == 0 && k >= 1 && kn < n_chunks) issue(kn, pre);
         }
         kbase += uint32_t(n_chunks);
         return;
@@ -626,37 +636,15 @@ __device__ __forceinline__ void fwd_tile_ws(const FwdArgs &a, int dtile, int tti
         const int ps = int(kg % Q);
         mbar_wait_bounded(&full_p[ps], (kg / Q) & 1u, a.err);
         const unsigned char *pb = pslot0 + ps * pslot_bytes;
-        const Acc *Pl = reinterpret_cast<const Acc *>(pb) + lb;
         const uint16_t *poffs =
             reinterpret_cast<const uint16_t *>(pb + a.p_elems * int(sizeof(Acc))) + wd * DPT;
-        const int c0 = k * a.cch;
-        const int ng = (min(a.cch, a.C - c0) + kSbG - 1) / kSbG;
-        for (int g = 0; g < ng; ++g) {
-            int o[DPT];
-            load_offsets<DPT>(poffs + g * a.Dt, o);
-#pragma unroll
-            for (int i = 0; i < DPT; ++i) {
-                const Acc *src = Pl + o[i];
-#pragma unroll
-                for (int j = 0; j < SPT; ++j) acc[i][j] += src[32 * j];
-            }
-        }
+        const int ng = (min(a.cch, a.C - k * a.cch) + kSbG - 1) / kSbG;
+        sb_trials<Acc, DPT, SPT>(acc, reinterpret_cast<const Acc *>(pb) + lb, poffs, a.Dt, ng);
         __syncwarp();
         if (lane == 0) mbar_arrive(&empty_p[ps]);
     }
     kbase += uint32_t(n_chunks);
-
-    Acc *out = static_cast<Acc *>(a.out);
-#pragma unroll
-    for (int i = 0; i < DPT; ++i) {
-        const int d = dtile * a.Dt + wd * DPT + i;
-        if (d >= a.D) continue;
-        Acc *orow = out + ((long long)b * a.D + d) * a.S + t0 + lb;
-        const long long tmax = a.S - t0 - lb;
-#pragma unroll
-        for (int j = 0; j < SPT; ++j)
-            if (32 * j < tmax) orow[32 * j] = acc[i][j];
-    }
+    store_lane_strided<Acc, DPT, SPT>(a, acc, dtile, b, t0, wd, lb);
 }
 
 // Dispatches a tile to the kind's body.

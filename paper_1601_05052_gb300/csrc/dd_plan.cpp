@@ -201,13 +201,14 @@ dd_status build_fwd_tables(dd_plan_s *p, const dd_variant &v, FwdTables *out) {
     t.stage_elems = static_cast<int>(stage_max);
     // 64 spare elements: register-window loads of a warp never leave the slot
     t.stage_data_bytes = static_cast<int>(round_up((stage_max + 64) * elt, 16));
+    // per slot after the window data: the chunk's tables, then its weights
     if (sb) {
         const int gpc = cch / kSbGroup;
         t.stage_offs_bytes = static_cast<int>(round_up(int64_t(gpc) * t.Dt * 2, 16)) +
-                             gpc * kSbPatterns * 32;
+                             gpc * kSbPatterns * 32 + cch * 4;
         t.p_elems = static_cast<int>(round_up(p_max + 64, 4));
     } else {
-        t.stage_offs_bytes = static_cast<int>(round_up(int64_t(cch) * t.Dt * 2, 16));
+        t.stage_offs_bytes = static_cast<int>(round_up(int64_t(cch) * t.Dt * 2, 16)) + cch * 4;
     }
     size_t p_bytes = 0;
     if (v.kind == 2) p_bytes = size_t(2) * t.p_elems * 4;
