@@ -10,8 +10,10 @@ the C ABI's dd_execute. Prints ONE JSON line (rank 0).
             every rank dedisperses its own beam, weak scaling)
   e2e       the same metric through dd_execute_host: pinned host input ->
             device -> kernel -> host output, every step
-  roofline  the forward kernel against the FP32 ALU peak (it is issue/ALU
-            bound: ~150 adds per compulsory HBM byte), plus its HBM fraction
+  roofline  the forward kernel's algorithmic adds (B*D*S*C) per second
+            against the FP32 ALU peak: with ~150 adds per compulsory HBM byte
+            the brute-force method is bound by arithmetic, not HBM; the HBM
+            fraction is reported beside it
   extras    8-bit / FP16 batched forms of the uneven-beam workload against
             plain FP32 launches of the same workload, the HBM-bound 96-beam
             FP32 point, and the differentiable workload's forward+backward
@@ -20,8 +22,10 @@ the C ABI's dd_execute. Prints ONE JSON line (rank 0).
 workload (the paper publishes no code to run).
 """
 import argparse
+import hashlib
 import json
 import os
+import re
 import statistics
 import subprocess
 import sys
@@ -34,6 +38,13 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "DM-trial·samples/s"
+# Sources that define the timed forward kernel; the DRAM traffic recorded in
+# profiles/ is only reported while they are unchanged.
+KERNEL_SOURCES = ["paper_1601_05052_gb300/csrc/dd_fwd_tile.cuh",
+                  "paper_1601_05052_gb300/csrc/dd_fwd.cu",
+                  "paper_1601_05052_gb300/csrc/dd_ptx.cuh",
+                  "paper_1601_05052_gb300/csrc/dd_plan.cpp"]
+TRAFFIC_PROFILE = "profiles/fwd_survey_f32.md"
 UNIT = "DM-trial·samples/s"
 WORKLOAD = "cfg2"
 L2_FLUSH_BYTES = 256 << 20
@@ -58,6 +69,32 @@ def _peaks():
             return json.load(f), "measured"
     except OSError:
         return {"hbm_gbs": 6800.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+def kernel_hash():
+    h = hashlib.sha256()
+    for f in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def recorded_traffic(variant):
+    """DRAM bytes per launch of the forward kernel from the committed ncu
+    summary, or None if the kernel sources or the variant changed since."""
+    try:
+        text = open(os.path.join(ROOT, TRAFFIC_PROFILE)).read()
+    except OSError:
+        return None
+    m_hash = re.search(r"kernel source hash: ([0-9a-f]{16})", text)
+    m_var = re.search(r"variant: (\{[^}]*\})", text)
+    m_rd = re.search(r"dram__bytes_read\.sum: ([0-9.]+) MB", text)
+    m_wr = re.search(r"dram__bytes_write\.sum: ([0-9.]+) MB", text)
+    if not (m_hash and m_var and m_rd and m_wr) or m_hash.group(1) != kernel_hash():
+        return None
+    if json.loads(m_var.group(1)) != variant:
+        return None
+    return (float(m_rd.group(1)) + float(m_wr.group(1))) * 1e6
 
 
 # ---------------------------------------------------------------- clocks
@@ -291,6 +328,7 @@ def run_ours(args):
 
     import synth
     from paper_1601_05052_gb300 import Plan
+    from paper_1601_05052_gb300.shard import max_over_ranks
 
     peaks, peaks_kind = _peaks()
     s = synth.setup(WORKLOAD)
@@ -320,11 +358,8 @@ def run_ours(args):
     clocks = clk.stop()
     if world > 1:
         dist.barrier()
-    total_ms = float(sum(times))
-    if world > 1:
-        t = torch.tensor([total_ms], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
+    # a step lasts as long as the slowest rank's
+    total_ms = max_over_ranks(float(sum(times)), device="cuda")
     ms = total_ms / args.steps
     units = s.batch * s.n_dm * s.n_out
     value = world * units / (ms * 1e-3)
@@ -353,7 +388,10 @@ def run_ours(args):
                        "l2": "flushed before every step (256 MB write outside the timed events)",
                        "variant": plan.variant},
             "roofline": {"bound": "alu", "achieved": achieved, "peak": alu_peak,
-                         "unit": "TFLOP/s", "frac": achieved / alu_peak, "traffic": None,
+                         "unit": "TFLOP/s", "frac": achieved / alu_peak,
+                         "traffic": recorded_traffic(plan.variant),
+                         "traffic_note": "DRAM bytes per launch (ncu, %s); compulsory %d"
+                                         % (TRAFFIC_PROFILE, comp_bytes),
                          "peak_kind": "derived: %d SMs x 128 FP32 lanes x %.0f MHz (%s max clock)"
                                       % (n_sm, peaks.get("sm_max_mhz", 2070.0), peaks_kind),
                          "op": "one FP32 add/FMA per channel per output (the paper's flop)",
