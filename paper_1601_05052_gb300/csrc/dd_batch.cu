@@ -33,7 +33,7 @@ struct BatchArgs {
 };
 
 template <int KIND, typename T, int DPT, int SPT>
-__global__ void __launch_bounds__(KIND == 3 ? 384 : 256, KIND == 3 ? 2 : 1)
+__global__ void __launch_bounds__(KIND == 3 ? 384 : (KIND == 2 ? 288 : 256), KIND >= 2 ? 2 : 1)
     dd_fwd_persistent_kernel(const BatchArgs ba) {
     extern __shared__ __align__(128) unsigned char smem[];
     __shared__ long long s_item;
@@ -147,7 +147,7 @@ dd_status configure(dd_batch_s *bt, const dd_variant &v) {
         smem = std::max(smem, t.smem_bytes);
         tabs.push_back(t);
     }
-    const int block = 32 * (v.warps_dm * v.warps_time + (v.kind == 3 ? kWsBuilders : 0));
+    const int block = 32 * (v.warps_dm * v.warps_time + extra_warps(v.kind));
     const int occ = pf.occupancy(block, smem);
     if (occ < 1) {
         for (auto &x : tabs) free_fwd_tables(&x);

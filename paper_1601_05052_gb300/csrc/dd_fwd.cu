@@ -13,7 +13,7 @@
 namespace dd {
 
 template <int KIND, typename T, int DPT, int SPT>
-__global__ void __launch_bounds__(KIND == 3 ? 384 : 256, KIND == 3 ? 2 : 1)
+__global__ void __launch_bounds__(KIND == 3 ? 384 : (KIND == 2 ? 288 : 256), KIND >= 2 ? 2 : 1)
     dd_fwd_kernel(const FwdArgs a) {
     extern __shared__ __align__(128) unsigned char smem[];
     uint64_t *bars = reinterpret_cast<uint64_t *>(smem);
@@ -105,7 +105,7 @@ dd_status launch_forward(dd_plan_s *p, const FwdTables &t, const void *in, const
     a.p_elems = t.p_elems;
     a.err = p->d_err;
     dim3 grid(unsigned(t.n_dtiles), unsigned(t.n_ttiles), unsigned(p->B));
-    dim3 block(unsigned(32 * (t.v.warps_dm * t.v.warps_time + (t.v.kind == 3 ? kWsBuilders : 0))));
+    dim3 block(unsigned(32 * (t.v.warps_dm * t.v.warps_time + extra_warps(t.v.kind))));
     cudaError_t e = fn(a, grid, block, t.smem_bytes, st);
     if (e != cudaSuccess) return cuda_fail(e, "forward launch");
     return DD_OK;

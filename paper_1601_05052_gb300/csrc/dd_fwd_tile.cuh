@@ -29,7 +29,8 @@
 //    so the CTA builds each pattern's weighted 4-channel partial series in
 //    shared memory once per chunk and the lane-strided trial loop adds one
 //    partial value per group instead of one input value per channel (the
-//    same sums, associated per group). One CTA barrier per chunk.
+//    same sums, associated per group). A dedicated producer warp stages the
+//    chunks; the compute warps meet at one named barrier per chunk.
 //  kind 3, warp-specialised sub-band: kind 2's arithmetic with 4 extra
 //    builder warps; mbarriers on the staging slots and on 3 partial-sum
 //    slots replace every CTA-wide barrier.
@@ -57,6 +58,11 @@ constexpr int kSbG = 4;
 constexpr int kSbP = 8;
 constexpr int kWsBuilders = 4;
 constexpr int kWsPSlots = 3;
+
+// Warps a CTA has beyond its warps_dm * warps_time trial warps.
+__host__ __device__ constexpr int extra_warps(int kind) {
+    return kind == 3 ? kWsBuilders : (kind == 2 ? 1 : 0);
+}
 
 template <typename T>
 struct Elem;
@@ -309,15 +315,17 @@ struct RegWindow {
     }
 };
 
-// Barriers: kinds 0-2 use full[s] = bars[s] (producer arrival + bytes) and,
-// for kinds 0/1, empty[s] = bars[8 + s] (one arrival per warp). Kind 3 uses
+// Barriers: every kind uses full[s] = bars[s] (producer arrival + bytes) and
+// empty[s] = bars[8 + s]: one arrival per warp for kinds 0/1, one per chunk
+// for kind 2 (after its compute barrier), one per builder warp for kind 3,
+// which also uses
 // bars[4..6] / bars[12..14] for its partial-sum slots and counts builder
 // warps on the staging slots' empty barriers.
 template <int KIND>
 __device__ __forceinline__ void fwd_init_barriers(uint64_t *bars, int stages) {
     if (threadIdx.x == 0) {
         const int n_warps = int(blockDim.x >> 5);
-        const int releasers = KIND == 3 ? kWsBuilders : n_warps;
+        const int releasers = KIND == 3 ? kWsBuilders : (KIND == 2 ? 1 : n_warps);
         for (int s = 0; s < stages; ++s) {
             mbar_init(&bars[s], 1);
             mbar_init(&bars[8 + s], uint32_t(releasers));
@@ -416,18 +424,18 @@ __device__ __forceinline__ void fwd_tile(const FwdArgs &a, int dtile, int ttile,
 
 // ------------------------------------------------------------------ kinds 2 and 3
 
-// Builds one partial series: dst[u] = sum_{j<gn} wg[j] * raw[r[j] + u] for
-// u < L, lanes of a warp striding by 32 and each lane keeping 4 elements in
-// flight so the shared-memory loads overlap.
+// Builds part of one partial series: dst[u] = sum_{j<gn} wg[j] * raw[r[j] + u]
+// for u in [u0, u1), lanes of a warp striding by 32 and each lane keeping 4
+// elements in flight so the shared-memory loads overlap.
 template <typename T>
 __device__ __forceinline__ void sb_build(typename Elem<T>::Acc *dst, const T *raw,
                                          const int (&r)[4], const typename Elem<T>::W (&wg)[4],
-                                         int gn, int L, int lane) {
+                                         int gn, int u0, int u1, int lane) {
     using Acc = typename Elem<T>::Acc;
     if (gn == kSbG) {
         const T *r0 = raw + r[0], *r1 = raw + r[1], *r2 = raw + r[2], *r3 = raw + r[3];
-        int u = lane;
-        for (; u + 96 < L; u += 128) {
+        int u = u0 + lane;
+        for (; u + 96 < u1; u += 128) {
             Acc v[4];
 #pragma unroll
             for (int q = 0; q < 4; ++q) {
@@ -438,11 +446,11 @@ __device__ __forceinline__ void sb_build(typename Elem<T>::Acc *dst, const T *ra
 #pragma unroll
             for (int q = 0; q < 4; ++q) dst[u + 32 * q] = v[q];
         }
-        for (; u < L; u += 32)
+        for (; u < u1; u += 32)
             dst[u] = wg[0] * Elem<T>::val(r0[u]) + wg[1] * Elem<T>::val(r1[u]) +
                      wg[2] * Elem<T>::val(r2[u]) + wg[3] * Elem<T>::val(r3[u]);
     } else {  // the last group of a plan may hold fewer channels
-        for (int u = lane; u < L; u += 32) {
+        for (int u = u0 + lane; u < u1; u += 32) {
             Acc v = wg[0] * Elem<T>::val(raw[r[0] + u]);
 #pragma unroll
             for (int j = 1; j < kSbG; ++j)
@@ -452,24 +460,36 @@ __device__ __forceinline__ void sb_build(typename Elem<T>::Acc *dst, const T *ra
     }
 }
 
-// Builds the partial series of build entries e = first, first + step, ... of
-// one chunk (entry = group * kSbP + pattern).
+// Builds this warp's share of a chunk's partial series. The chunk's valid
+// build entries are compacted at its head and laid out back to back in the
+// partial-sum buffer, so the buffer's E elements are split evenly: worker
+// `part` of `parts` builds elements [E*part/parts, E*(part+1)/parts), touching
+// the one to few entries that overlap that range (found with one ballot).
 template <typename T>
-__device__ __forceinline__ void sb_build_entries(typename Elem<T>::Acc *P, const T *raw,
-                                                 const int4 *bd, const typename Elem<T>::W *sw,
-                                                 int ng, int first, int step, int lane) {
+__device__ __forceinline__ void sb_build_share(typename Elem<T>::Acc *P, const T *raw,
+                                               const int4 *bd, const typename Elem<T>::W *sw,
+                                               int n_slots, int part, int parts, int lane) {
     using Wt = typename Elem<T>::W;
-    for (int e = first; e < ng * kSbP; e += step) {
-        const int4 A = bd[2 * e];
-        if (A.y == 0) continue;
-        const int4 B = bd[2 * e + 1];
-        const int g = e / kSbP;
-        const int gn = B.z;
+    int4 A = make_int4(0, 0, 0, 0);
+    if (lane < n_slots) A = bd[2 * lane];
+    int end = A.x + A.y;  // entries are in buffer order: the last valid one ends at E
+#pragma unroll
+    for (int m = 16; m >= 1; m >>= 1) end = max(end, __shfl_xor_sync(0xffffffffu, end, m));
+    const int E = end;
+    const int i0 = int((long long)E * part / parts), i1 = int((long long)E * (part + 1) / parts);
+    unsigned mask = __ballot_sync(0xffffffffu, A.y > 0 && A.x < i1 && A.x + A.y > i0);
+    while (mask) {
+        const int e = __ffs(mask) - 1;
+        mask &= mask - 1;
+        const int4 Ae = bd[2 * e];
+        const int4 Be = bd[2 * e + 1];
+        const int gn = Be.z, g = Be.w;
         Wt wg[4];
 #pragma unroll
         for (int j = 0; j < 4; ++j) wg[j] = j < gn ? sw[g * kSbG + j] : Wt(0);
-        const int r[4] = {A.z, A.w, B.x, B.y};
-        sb_build<T>(P + A.x, raw, r, wg, gn, A.y, lane);
+        const int r[4] = {Ae.z, Ae.w, Be.x, Be.y};
+        const int u0 = max(i0, Ae.x) - Ae.x, u1 = min(i1, Ae.x + Ae.y) - Ae.x;
+        sb_build<T>(P + Ae.x, raw, r, wg, gn, u0, u1, lane);
     }
 }
 
@@ -492,33 +512,54 @@ __device__ __forceinline__ void sb_trials(Acc (&acc)[DPT][SPT], const Acc *Pl,
     }
 }
 
-// kind 2: sub-band partial sums. One CTA barrier per chunk separates the
-// build of the chunk's partial series from the trial loop; the partial-sum
-// buffer alternates between two halves by global chunk parity so a chunk's
-// build never overwrites what slower warps still read.
+// Barrier over the first n threads of the CTA (named barrier 1): the
+// compute warps of a kind-2 CTA synchronise without the producer warp.
+__device__ __forceinline__ void compute_barrier(int n) {
+    asm volatile("bar.sync 1, %0;" ::"r"(n) : "memory");
+}
+
+// kind 2: sub-band partial sums with a producer warp. Warps [0, NC) compute;
+// warp NC only stages chunks, running up to `stages` chunks ahead and
+// throttled by the slots' empty barriers (one arrival per chunk, made after
+// the compute warps' build barrier). Per chunk the compute warps build the
+// partial series (and copy the chunk's trial offsets next to them), meet at
+// a named barrier, release the staging slot and run the trial loop.
+// Partial-sum slots alternate by global chunk parity, so a chunk's build
+// never overwrites what slower warps still read.
 template <typename T, int DPT, int SPT>
 __device__ __forceinline__ void fwd_tile_sb(const FwdArgs &a, int dtile, int ttile, int b,
                                             uint64_t *bars, unsigned char *stage0,
                                             uint32_t &kbase) {
     using Acc = typename Elem<T>::Acc;
     using Wt = typename Elem<T>::W;
-    uint64_t *full = bars;
+    uint64_t *full = bars, *empty = bars + 8;
     const uint32_t S = uint32_t(a.stages);
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const int n_warps = int(blockDim.x >> 5);
-    const int wd = warp % a.warps_dm, wt = warp / a.warps_dm;
+    const int nc = int(blockDim.x >> 5) - 1;  // compute warps; warp nc produces
     const long long t0 = (long long)ttile * a.Ts;
     const int n_chunks = (a.C + a.cch - 1) / a.cch;
     const Stager<T> st = make_stager<T>(a, dtile, b, t0, stage0, true);
-    Acc *pbuf = reinterpret_cast<Acc *>(stage0 + S * st.stage_bytes);
-    auto slot_of = [&](int k) { return int((kbase + uint32_t(k)) % S); };
+    const uint32_t poffs_bytes = st.tab1_bytes;
+    const int pslot_bytes = a.p_elems * int(sizeof(Acc)) + int(poffs_bytes);
+    unsigned char *pslot0 = stage0 + S * st.stage_bytes;
 
-    if (warp == 0) {
-        const int pro = min(int(S), n_chunks);
-        for (int k = 0; k < pro; ++k)
-            st.issue(k, slot_of(k), st.desc(k, lane), &full[slot_of(k)], lane);
+    if (warp == nc) {
+        // ---------------- producer warp
+        int4 dsc = st.desc(0, lane);
+        for (int k = 0; k < n_chunks; ++k) {
+            const uint32_t kg = kbase + uint32_t(k);
+            const int slot = int(kg % S);
+            const int4 next = (k + 1 < n_chunks) ? st.desc(k + 1, lane) : make_int4(0, 0, 0, 0);
+            if (kg >= S) mbar_wait_bounded(&empty[slot], ((kg / S) - 1u) & 1u, a.err);
+            st.issue(k, slot, dsc, &full[slot], lane);
+            dsc = next;
+        }
+        kbase += uint32_t(n_chunks);
+        return;
     }
 
+    // ---------------- compute warps
+    const int wd = warp % a.warps_dm, wt = warp / a.warps_dm;
     Acc acc[DPT][SPT];
 #pragma unroll
     for (int i = 0; i < DPT; ++i)
@@ -529,24 +570,24 @@ __device__ __forceinline__ void fwd_tile_sb(const FwdArgs &a, int dtile, int tti
     for (int k = 0; k < n_chunks; ++k) {
         const uint32_t kg = kbase + uint32_t(k);
         const int slot = int(kg % S);
-        const int kn = k - 1 + int(S);
-        int4 pre = make_int4(0, 0, 0, 0);
-        if (warp == 0 && k >= 1 && kn < n_chunks) pre = st.desc(kn, lane);
         mbar_wait_bounded(&full[slot], (kg / S) & 1u, a.err);
         const unsigned char *sb = stage0 + slot * st.stage_bytes;
         const T *raw = reinterpret_cast<const T *>(sb);
-        const uint16_t *poffs = reinterpret_cast<const uint16_t *>(sb + a.stage_data_bytes);
-        const int4 *bd = reinterpret_cast<const int4 *>(sb + a.stage_data_bytes + st.tab1_bytes);
+        const int4 *bd = reinterpret_cast<const int4 *>(sb + a.stage_data_bytes + poffs_bytes);
         const Wt *sw = reinterpret_cast<const Wt *>(sb + a.stage_data_bytes + st.tab_bytes);
-        Acc *P = pbuf + (kg & 1u) * a.p_elems;
+        unsigned char *pb = pslot0 + (kg & 1u) * pslot_bytes;
+        Acc *P = reinterpret_cast<Acc *>(pb);
+        uint16_t *poffs = reinterpret_cast<uint16_t *>(pb + a.p_elems * int(sizeof(Acc)));
         const int ng = (min(a.cch, a.C - k * a.cch) + kSbG - 1) / kSbG;
 
-        sb_build_entries<T>(P, raw, bd, sw, ng, warp, n_warps, lane);
-        __syncthreads();
-        // every warp has finished the trial loop of chunk k-1 (it precedes the
-        // build of chunk k), so that chunk's slot, tables included, is free
-        if (warp == 0 && k >= 1 && kn < n_chunks)
-            st.issue(kn, slot_of(kn), pre, &full[slot_of(kn)], lane);
+        sb_build_share<T>(P, raw, bd, sw, ng * kSbP, warp, nc, lane);
+        {  // the chunk's trial offsets move next to its partial sums
+            const uint32_t *src = reinterpret_cast<const uint32_t *>(sb + a.stage_data_bytes);
+            uint32_t *dst = reinterpret_cast<uint32_t *>(poffs);
+            for (int i = tid; i < int(poffs_bytes / 4); i += nc * 32) dst[i] = src[i];
+        }
+        compute_barrier(nc * 32);
+        if (tid == 0) mbar_arrive(&empty[slot]);  // nothing reads this staging slot any more
         sb_trials<Acc, DPT, SPT>(acc, P + lb, poffs + wd * DPT, a.Dt, ng);
     }
     kbase += uint32_t(n_chunks);
@@ -604,8 +645,8 @@ __device__ __forceinline__ void fwd_tile_ws(const FwdArgs &a, int dtile, int tti
             const Wt *sw = reinterpret_cast<const Wt *>(sb + a.stage_data_bytes + st.tab_bytes);
             unsigned char *pb = pslot0 + ps * pslot_bytes;
             const int ng = (min(a.cch, a.C - k * a.cch) + kSbG - 1) / kSbG;
-            sb_build_entries<T>(reinterpret_cast<Acc *>(pb), raw, bd, sw, ng, bw, kWsBuilders,
-                                lane);
+            sb_build_share<T>(reinterpret_cast<Acc *>(pb), raw, bd, sw, ng * kSbP, bw, kWsBuilders,
+                              lane);
             if (bw == 0) {  // the trial offsets travel with the partial sums
                 const uint32_t *src = reinterpret_cast<const uint32_t *>(sb + a.stage_data_bytes);
                 uint32_t *dsto = reinterpret_cast<uint32_t *>(pb + a.p_elems * int(sizeof(Acc)));

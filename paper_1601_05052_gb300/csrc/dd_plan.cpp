@@ -184,15 +184,20 @@ dd_status build_fwd_tables(dd_plan_s *p, const dd_variant &v, FwdTables *out) {
                 p_max = std::max(p_max, ch.p_elems);
                 const int g0 = c0 / kSbGroup;
                 const int ng = int(ch.poffs.size()) / t.Dt;
+                // build entries of the chunk, compacted: the valid (group, pattern)
+                // entries first, in partial-buffer order, each tagged with its
+                // group; the rest keep length 0
+                size_t at = (size_t(k) * G_pad + g0) * kSbPatterns * 2;
                 for (int g = 0; g < ng; ++g) {
                     for (int i = 0; i < t.Dt; ++i)
                         offs[(size_t(k) * G_pad + g0 + g) * t.Dt + i] =
                             static_cast<uint16_t>(ch.poffs[size_t(g) * t.Dt + i]);
                     for (int q = 0; q < kSbPatterns; ++q) {
                         const int *bd = &ch.bdesc[(size_t(g) * kSbPatterns + q) * 8];
-                        const size_t at = ((size_t(k) * G_pad + g0 + g) * kSbPatterns + q) * 2;
+                        if (bd[1] == 0) continue;
                         bdesc[at] = make_int4(bd[0], bd[1], bd[2], bd[3]);
-                        bdesc[at + 1] = make_int4(bd[4], bd[5], bd[6], bd[7]);
+                        bdesc[at + 1] = make_int4(bd[4], bd[5], bd[6], g);
+                        at += 2;
                     }
                 }
             }
@@ -211,7 +216,8 @@ dd_status build_fwd_tables(dd_plan_s *p, const dd_variant &v, FwdTables *out) {
         t.stage_offs_bytes = static_cast<int>(round_up(int64_t(cch) * t.Dt * 2, 16)) + cch * 4;
     }
     size_t p_bytes = 0;
-    if (v.kind == 2) p_bytes = size_t(2) * t.p_elems * 4;
+    if (v.kind == 2)  // 2 partial-sum slots, each with the chunk's trial offsets
+        p_bytes = size_t(2) * (size_t(t.p_elems) * 4 + size_t(cch / kSbGroup) * t.Dt * 2);
     if (v.kind == 3)  // 3 partial-sum slots, each with the chunk's trial offsets
         p_bytes = size_t(3) * (size_t(t.p_elems) * 4 + size_t(cch / kSbGroup) * t.Dt * 2);
     t.smem_bytes = 128 + size_t(v.stages) * (t.stage_data_bytes + t.stage_offs_bytes) + p_bytes;
