@@ -283,19 +283,22 @@ def _extras(torch, flush, peaks, steps):
     # HBM-bound point: 96 beams of the 64-channel setup in FP32
     s = synth.setup("cfg1x96")
     p = Plan.from_setup(s)
+    p.tune(budget_ms=8000)
     x = rand_input(p, 7, "f32")
     w = torch.ones(p.n_chan, device="cuda")
     o = torch.empty(p.out_shape, device="cuda")
     t = statistics.median(_time_steps(lambda: p.execute(x, w, o), n_rep, 2, flush, torch))
     comp = (x.numel() * 4 + o.numel() * 4) / (t * 1e-3) / 1e9
     out["f32_96beams_64ch"] = {"value": s.batch * s.n_dm * s.n_out / (t * 1e-3), "unit": UNIT,
-                               "ms": t, "effective_hbm_gbs": comp,
+                               "ms": t, "variant": p.variant, "effective_hbm_gbs": comp,
                                "hbm_frac": comp / peaks["hbm_gbs"]}
     del x, o
 
     # differentiable workload: forward + backward (grad_in and grad_w)
     s = synth.setup("cfg5")
     p = Plan.from_setup(s)
+    p.tune(budget_ms=8000)
+    p.tune_adjoint(budget_ms=8000)
     x = rand_input(p, 9, "f32").requires_grad_(True)
     w = torch.ones(p.n_chan, device="cuda", requires_grad=True)
 

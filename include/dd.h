@@ -191,6 +191,11 @@ dd_status dd_grad_w_noalloc(dd_plan plan, const float *d_gout, const float *d_in
  * fills *rep (nullable). budget_ms bounds the sweep (0 = no bound). */
 dd_status dd_tune(dd_plan plan, int32_t budget_ms, dd_tune_report *rep);
 
+/* Tunes the kernel variant of the adjoint's transposed dedispersion (the
+ * gather runs the forward kernels with channels and trials swapped; see
+ * dd_adjoint). Builds the adjoint's buffers if they do not exist yet. */
+dd_status dd_tune_adjoint(dd_plan plan, int32_t budget_ms, dd_tune_report *rep);
+
 /* ---- Batched uneven setups (many beams of several observation setups) ----
  * A batch groups n plans (different C, D, S, input types). dd_batch_execute
  * runs every plan's forward in ONE persistent kernel launch whose CTAs pull
@@ -213,6 +218,12 @@ dd_status dd_batch_tune(dd_batch batch, int32_t budget_ms, dd_tune_report *rep);
 void dd_batch_destroy(dd_batch batch);
 
 /* ---- Diagnostics ---------------------------------------------------------- */
+/* Failure-path check: enqueues one CTA that waits on a shared-memory
+ * barrier nothing will complete, with a wait budget of budget_us
+ * microseconds (1..2000000). When the budget runs out the kernel records
+ * DD_ERR_TIMEOUT in the plan's device error word and returns, so the
+ * context stays usable; dd_plan_check_device then reports it. */
+dd_status dd_debug_wait_timeout(dd_plan plan, int32_t budget_us, void *stream);
 /* Synchronises the device, reads and clears the plan's device error word:
  * DD_OK, DD_ERR_TIMEOUT (a bounded wait ran out) or DD_ERR_DEVICE. */
 dd_status dd_plan_check_device(dd_plan plan);

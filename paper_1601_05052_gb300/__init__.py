@@ -145,6 +145,12 @@ class Plan:
         _lib.check(_lib_().dd_tune(self._h, int(budget_ms), ctypes.byref(r)))
         return r.as_dict()
 
+    def tune_adjoint(self, budget_ms=0):
+        """Tunes the kernel variant the adjoint's transposed gather runs."""
+        r = TuneReport()
+        _lib.check(_lib_().dd_tune_adjoint(self._h, int(budget_ms), ctypes.byref(r)))
+        return r.as_dict()
+
     def check_device(self):
         _lib.check(_lib_().dd_plan_check_device(self._h))
 

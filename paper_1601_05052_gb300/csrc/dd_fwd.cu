@@ -23,6 +23,17 @@ __global__ void __launch_bounds__(KIND == 3 ? 384 : (KIND == 2 ? 288 : 256), KIN
                                     kbase);
 }
 
+// One CTA waits on an mbarrier that nothing arrives at, bounded by budget_ns.
+__global__ void dd_wait_timeout_kernel(int *err, unsigned long long budget_ns) {
+    __shared__ __align__(8) uint64_t bar;
+    if (threadIdx.x == 0) {
+        mbar_init(&bar, 1);
+        fence_barrier_init();
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) mbar_wait_bounded(&bar, 0u, err, budget_ns);
+}
+
 namespace {
 
 using FwdLaunchFn = cudaError_t (*)(const FwdArgs &, dim3, dim3, size_t, cudaStream_t);
@@ -122,6 +133,15 @@ dd_status dd_execute(dd_plan p, const void *d_in, const void *d_w, void *d_out, 
     if (!aligned16(d_in) || !aligned16(d_w) || !aligned16(d_out))
         return fail(DD_ERR_ARG, "device pointers must be 16-byte aligned");
     return launch_forward(p, p->fwd, d_in, d_w, d_out, static_cast<cudaStream_t>(stream));
+}
+
+dd_status dd_debug_wait_timeout(dd_plan p, int32_t budget_us, void *stream) {
+    if (!p || budget_us < 1 || budget_us > 2000000) return fail(DD_ERR_ARG, "bad argument");
+    dd_wait_timeout_kernel<<<1, 32, 0, static_cast<cudaStream_t>(stream)>>>(
+        p->d_err, (unsigned long long)budget_us * 1000ull);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(e, "timeout probe launch");
+    return DD_OK;
 }
 
 dd_status dd_execute_host(dd_plan p, const void *h_in, const void *h_w, void *h_out,

@@ -58,20 +58,18 @@ struct FwdTables {
 constexpr int kSbGroup = 4;
 constexpr int kSbPatterns = 8;
 
-// Tables of the adjoint (gather) kernel: the roles of channels and trials
-// swap. A CTA owns a tile of Ct channels by Tt input samples and stages, per
-// trial d, the cotangent samples g[d][tau0 - A_d, tau0 - A_d + len_d) with
-// A_d = smax_d rounded up to 4 (smax_d/smin_d over the channel tile).
-//   adesc[k][d] = {A_d, len_d, smem_off, 0}
-//   aoffs[k][d][j] = smem_off + A_d - shift[d][k*Ct + j]
-struct AdjTables {
-    int Ct = 0, Tt = 0, cpt = 0, spt = 0, wc = 0, wt = 0, dch = 0;
-    int n_ctiles = 0, n_ttiles = 0, D_pad = 0;
-    int stage_elems = 0;
-    size_t smem_bytes = 0;
-    int4 *d_desc = nullptr;
-    uint16_t *d_offs = nullptr;
-    float *d_part = nullptr;     // [n_ttiles][B][C] grad_w partial sums (scratch)
+// Adjoint state of a plan, built on first use: the transposed plan (D
+// "channels", C "trials", delays max_shift - shift, outputs over the padded
+// input rows), the zero-bordered copy of the cotangent it reads, unit
+// weights, per (beam, channel) grad_w partial sums, and a G scratch buffer
+// for calls that want grad_w without grad_in.
+struct AdjState {
+    dd_plan_s *plan = nullptr;
+    int32_t M = 0;
+    float *gpad = nullptr;  // [B][D][plan->stride]
+    float *ones = nullptr;  // [D]
+    float *part = nullptr;  // [B][C]
+    float *gscr = nullptr;  // [B][C][stride], allocated when first needed
 };
 
 }  // namespace dd
@@ -88,7 +86,7 @@ struct dd_plan_s {
     size_t smem_optin = 0;
 
     dd::FwdTables fwd;
-    dd::AdjTables adj;
+    dd::AdjState adj;
     int32_t *d_shifts = nullptr;  // device copy of `shifts`
     int *d_err = nullptr;         // device error word (dd::kErr* bits)
 
@@ -122,8 +120,8 @@ dd_status launch_forward(dd_plan_s *p, const FwdTables &t, const void *in, const
                          void *out, cudaStream_t st);
 
 // Adjoint
-dd_status ensure_adj_tables(dd_plan_s *p);
-void free_adj_tables(AdjTables *t);
+dd_status ensure_adj_state(dd_plan_s *p);
+void free_adj_state(AdjState *a);
 dd_status launch_adjoint(dd_plan_s *p, const float *g, const float *w, const float *in,
                          float *gin, float *gw, cudaStream_t st);
 

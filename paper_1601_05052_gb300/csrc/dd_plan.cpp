@@ -396,7 +396,7 @@ dd_status dd_plan_create_from_shifts(dd_plan *out, int32_t n_chan, int32_t n_dm,
 void dd_plan_destroy(dd_plan p) {
     if (!p) return;
     free_fwd_tables(&p->fwd);
-    free_adj_tables(&p->adj);
+    free_adj_state(&p->adj);
     if (p->d_err) cudaFree(p->d_err);
     if (p->d_shifts) cudaFree(p->d_shifts);
     if (p->h_in_dev) cudaFree(p->h_in_dev);

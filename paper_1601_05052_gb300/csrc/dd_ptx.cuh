@@ -73,13 +73,14 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
 
 // Bounded wait for the phase with the given parity to complete. Returns false
 // (and sets kErrWaitTimeout in *err) if the budget ran out.
-__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity, int *err) {
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity, int *err,
+                                                  unsigned long long budget_ns = kWaitBudgetNs) {
     if (mbar_try_wait(bar, parity)) return true;
     const unsigned long long t0 = globaltimer_ns();
     for (;;) {
         for (int i = 0; i < 64; ++i)
             if (mbar_try_wait(bar, parity)) return true;
-        if (globaltimer_ns() - t0 > kWaitBudgetNs) {
+        if (globaltimer_ns() - t0 > budget_ns) {
             if (err) atomicOr(err, kErrWaitTimeout);
             return false;
         }

@@ -172,3 +172,21 @@ def test_survey_scale_f32_sampled():
         col = out[0, :, t0].cpu().numpy()
         assert col[d] > 0.5 * a * s.n_chan
     plan.check_device()
+
+
+def test_bounded_wait_reports_timeout_and_context_survives():
+    """A kernel waiting on a barrier nothing completes gives up after its
+    budget, the host reads DD_ERR_TIMEOUT, and the next launch still works."""
+    import ctypes
+    from paper_1601_05052_gb300 import DDError, _lib
+    rng = np.random.default_rng(12)
+    sh, x, w = random_case(rng, 1, 8, 8, 300, 20, "f32")
+    plan = Plan(shifts=sh, n_out=300, batch=1)
+    plan.check_device()
+    st = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    _lib.check(_lib.load().dd_debug_wait_timeout(plan._h, 50000, st))  # 50 ms budget
+    with pytest.raises(DDError) as e:
+        plan.check_device()
+    assert e.value.status == 5  # DD_ERR_TIMEOUT
+    plan.check_device()  # the error word was cleared
+    check_full(plan, x, w, sh, "f32", "after timeout")
