@@ -34,6 +34,28 @@ __global__ void dd_wait_timeout_kernel(int *err, unsigned long long budget_ns) {
     if (threadIdx.x == 0) mbar_wait_bounded(&bar, 0u, err, budget_ns);
 }
 
+// Copies n 16-byte words with all SMs (used to pull pinned host memory over
+// the CPU-GPU link at the link's rate rather than one copy engine's).
+__global__ void dd_copy16_kernel(uint4 *__restrict__ dst, const uint4 *__restrict__ src,
+                                 size_t n) {
+    for (size_t i = blockIdx.x * size_t(blockDim.x) + threadIdx.x; i < n;
+         i += size_t(gridDim.x) * blockDim.x)
+        dst[i] = src[i];
+}
+
+// Device-side address of a page-locked host buffer, or null for pageable or
+// device memory.
+const void *mapped_host_ptr(const void *p) {
+    cudaPointerAttributes at{};
+    if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    if (at.type != cudaMemoryTypeHost || !at.devicePointer) return nullptr;
+    return at.devicePointer;
+}
+void *mapped_host_ptr(void *p) { return const_cast<void *>(mapped_host_ptr(static_cast<const void *>(p))); }
+
 namespace {
 
 using FwdLaunchFn = cudaError_t (*)(const FwdArgs &, dim3, dim3, size_t, cudaStream_t);
@@ -151,23 +173,38 @@ dd_status dd_execute_host(dd_plan p, const void *h_in, const void *h_w, void *h_
     const size_t in_bytes = size_t(p->B) * p->C * p->stride * elt_bytes(p->dtype);
     const size_t w_bytes = size_t(p->C) * 4;
     const size_t out_bytes = size_t(p->B) * p->D * p->S * 4;
+    // Pinned (page-locked, mapped) host buffers are reachable from the GPU over
+    // the CPU-GPU link: the input is pulled by an SM copy kernel and the
+    // forward kernel writes its output straight into host memory, so no
+    // output copy follows it. Pageable buffers go through device mirrors.
+    const void *in_dev = mapped_host_ptr(h_in);
+    void *out_dev = mapped_host_ptr(h_out);
     {
         std::lock_guard<std::mutex> lk(p->mu);
         cudaError_t e = cudaSuccess;
         if (!p->h_in_dev) e = cudaMalloc(&p->h_in_dev, in_bytes);
         if (e == cudaSuccess && !p->h_w_dev) e = cudaMalloc(&p->h_w_dev, w_bytes);
-        if (e == cudaSuccess && !p->h_out_dev) e = cudaMalloc(&p->h_out_dev, out_bytes);
+        if (e == cudaSuccess && !out_dev && !p->h_out_dev) e = cudaMalloc(&p->h_out_dev, out_bytes);
         if (e != cudaSuccess) return cuda_fail(e, "cudaMalloc(host mirrors)");
     }
-    cudaError_t e = cudaMemcpyAsync(p->h_in_dev, h_in, in_bytes, cudaMemcpyHostToDevice, st);
+    cudaError_t e = cudaSuccess;
+    if (in_dev && aligned16(in_dev)) {
+        const int grid = 4 * p->sm_count;
+        dd_copy16_kernel<<<grid, 256, 0, st>>>(static_cast<uint4 *>(p->h_in_dev),
+                                               static_cast<const uint4 *>(in_dev), in_bytes / 16);
+        e = cudaGetLastError();
+    } else {
+        e = cudaMemcpyAsync(p->h_in_dev, h_in, in_bytes, cudaMemcpyHostToDevice, st);
+    }
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(p->h_w_dev, h_w, w_bytes, cudaMemcpyHostToDevice, st);
-    if (e != cudaSuccess) return cuda_fail(e, "cudaMemcpyAsync(H2D)");
-    dd_status s = launch_forward(p, p->fwd, p->h_in_dev, p->h_w_dev, p->h_out_dev, st);
+    if (e != cudaSuccess) return cuda_fail(e, "input upload");
+    void *out = out_dev ? out_dev : p->h_out_dev;
+    dd_status s = launch_forward(p, p->fwd, p->h_in_dev, p->h_w_dev, out, st);
     if (s != DD_OK) return s;
-    e = cudaMemcpyAsync(h_out, p->h_out_dev, out_bytes, cudaMemcpyDeviceToHost, st);
+    if (!out_dev) e = cudaMemcpyAsync(h_out, p->h_out_dev, out_bytes, cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
-    if (e != cudaSuccess) return cuda_fail(e, "cudaMemcpyAsync(D2H)/sync");
+    if (e != cudaSuccess) return cuda_fail(e, "output download / sync");
     return DD_OK;
 }
 

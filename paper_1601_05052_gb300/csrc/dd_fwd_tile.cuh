@@ -134,6 +134,21 @@ __device__ __forceinline__ void load_offsets(const uint16_t *p, int (&o)[DPT]) {
     }
 }
 
+// Packed FP32 pair arithmetic of sm_100-class GPUs (one instruction for two
+// lanes' worth of adds / fmas): a += b and d = a * b + c element-wise.
+__device__ __forceinline__ void add2(float &a0, float &a1, float b0, float b1) {
+    asm("{\n\t.reg .b64 x, y;\n\tmov.b64 x, {%0, %1};\n\tmov.b64 y, {%2, %3};\n\t"
+        "add.rn.f32x2 x, x, y;\n\tmov.b64 {%0, %1}, x;\n\t}"
+        : "+f"(a0), "+f"(a1)
+        : "f"(b0), "f"(b1));
+}
+__device__ __forceinline__ void fma2(float &d0, float &d1, float a0, float a1, float b0, float b1) {
+    asm("{\n\t.reg .b64 x, y, z;\n\tmov.b64 x, {%2, %3};\n\tmov.b64 y, {%4, %5};\n\t"
+        "mov.b64 z, {%0, %1};\n\tfma.rn.f32x2 z, x, y, z;\n\tmov.b64 {%0, %1}, z;\n\t}"
+        : "+f"(d0), "+f"(d1)
+        : "f"(a0), "f"(a1), "f"(b0), "f"(b1));
+}
+
 // ------------------------------------------------------------------ staging
 
 // Per-tile staging context. Layout of a slot: [window data: stage_data_bytes]
@@ -437,11 +452,23 @@ __device__ __forceinline__ void sb_build(typename Elem<T>::Acc *dst, const T *ra
         int u = u0 + lane;
         for (; u + 96 < u1; u += 128) {
             Acc v[4];
+            if constexpr (std::is_same<Acc, float>::value) {
 #pragma unroll
-            for (int q = 0; q < 4; ++q) {
-                const int x = u + 32 * q;
-                v[q] = wg[0] * Elem<T>::val(r0[x]) + wg[1] * Elem<T>::val(r1[x]) +
-                       wg[2] * Elem<T>::val(r2[x]) + wg[3] * Elem<T>::val(r3[x]);
+                for (int q = 0; q < 4; q += 2) {  // two elements per packed instruction
+                    const int x = u + 32 * q, y = x + 32;
+                    v[q] = wg[0] * Elem<T>::val(r0[x]);
+                    v[q + 1] = wg[0] * Elem<T>::val(r0[y]);
+                    fma2(v[q], v[q + 1], wg[1], wg[1], Elem<T>::val(r1[x]), Elem<T>::val(r1[y]));
+                    fma2(v[q], v[q + 1], wg[2], wg[2], Elem<T>::val(r2[x]), Elem<T>::val(r2[y]));
+                    fma2(v[q], v[q + 1], wg[3], wg[3], Elem<T>::val(r3[x]), Elem<T>::val(r3[y]));
+                }
+            } else {
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    const int x = u + 32 * q;
+                    v[q] = wg[0] * Elem<T>::val(r0[x]) + wg[1] * Elem<T>::val(r1[x]) +
+                           wg[2] * Elem<T>::val(r2[x]) + wg[3] * Elem<T>::val(r3[x]);
+                }
             }
 #pragma unroll
             for (int q = 0; q < 4; ++q) dst[u + 32 * q] = v[q];
@@ -505,8 +532,14 @@ __device__ __forceinline__ void sb_trials(Acc (&acc)[DPT][SPT], const Acc *Pl,
 #pragma unroll
             for (int i = 0; i < DPT; ++i) {
                 const Acc *src = Pl + o[i];
+                if constexpr (std::is_same<Acc, float>::value && SPT % 2 == 0) {
 #pragma unroll
-                for (int j = 0; j < SPT; ++j) acc[i][j] += src[32 * j];
+                    for (int j = 0; j < SPT; j += 2)
+                        add2(acc[i][j], acc[i][j + 1], src[32 * j], src[32 * (j + 1)]);
+                } else {
+#pragma unroll
+                    for (int j = 0; j < SPT; ++j) acc[i][j] += src[32 * j];
+                }
             }
         }
     }

@@ -131,8 +131,16 @@ def test_execute_host_matches_device_path():
     hx = torch.from_numpy(x).pin_memory()
     hw = torch.from_numpy(w).pin_memory()
     hout = torch.empty(plan.out_shape, dtype=torch.float32).pin_memory()
-    plan.execute_host(hx, hw, hout)
+    plan.execute_host(hx, hw, hout)  # pinned: pulled and written over the CPU-GPU link
     assert torch.equal(dev, hout)
+    px = torch.from_numpy(x.copy())  # pageable: staged through device mirrors
+    pout = torch.zeros(plan.out_shape, dtype=torch.float32)
+    plan.execute_host(px, torch.from_numpy(w.copy()), pout)
+    assert torch.equal(dev, pout)
+    for _ in range(2):  # repeated calls reuse the mirrors
+        hout.zero_()
+        plan.execute_host(hx, hw, hout)
+        assert torch.equal(dev, hout)
 
 
 def test_tuned_variant_stays_correct():
