@@ -33,7 +33,8 @@ struct BatchArgs {
 };
 
 template <int KIND, typename T, int DPT, int SPT>
-__global__ void __launch_bounds__(KIND == 3 ? 384 : (KIND == 2 ? 288 : 256), KIND >= 2 ? 2 : 1)
+__global__ void __launch_bounds__(KIND == 3 ? 384 : (KIND == 2 ? 288 : 256),
+                      KIND == 2 ? (DPT * SPT <= 16 ? 3 : 2) : (KIND == 3 ? 2 : 1))
     dd_fwd_persistent_kernel(const BatchArgs ba) {
     extern __shared__ __align__(128) unsigned char smem[];
     __shared__ long long s_item;
