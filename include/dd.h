@@ -61,6 +61,7 @@ typedef enum {
 
 typedef struct dd_plan_s *dd_plan;
 typedef struct dd_batch_s *dd_batch;
+typedef struct dd_stream_s *dd_stream;
 
 /* Tile shape of the forward kernel (Section III-B's four parameters plus the
  * staging pipeline). A CTA computes dm_per_thread * warps_dm trial DMs by
@@ -188,7 +189,15 @@ dd_status dd_grad_w_noalloc(dd_plan plan, const float *d_gout, const float *d_in
 /* ---- Auto-tuning (Section IV-A / V-A) ------------------------------------
  * Times every compiled variant that fits this plan on scratch buffers it
  * allocates and frees itself, keeps the fastest as the plan's variant and
- * fills *rep (nullable). budget_ms bounds the sweep (0 = no bound). */
+ * fills *rep (nullable). budget_ms bounds the sweep (0 = no bound).
+ * Tuning cache: when the environment variable DD_TUNE_CACHE names a file,
+ * dd_tune appends one text line "<key> kind dpt spt warps_dm warps_time
+ * chans_per_stage stages" for the winner, the key being the device name,
+ * input type, n_chan, n_dm, n_out, batch and a hash of the delay table; plan
+ * creation (dd_plan_create, dd_plan_create_from_shifts) then starts from the
+ * last line whose key matches, so the sweep is an offline step, as the paper
+ * treats it. A missing or unreadable file, or a recorded variant that no
+ * longer fits, falls back to the built-in defaults silently. */
 dd_status dd_tune(dd_plan plan, int32_t budget_ms, dd_tune_report *rep);
 
 /* Tunes the kernel variant of the adjoint's transposed dedispersion (the
@@ -216,6 +225,23 @@ dd_status dd_batch_set_variant(dd_batch batch, const dd_variant *v);
  * buffers allocated and freed here); same report as dd_tune. */
 dd_status dd_batch_tune(dd_batch batch, int32_t budget_ms, dd_tune_report *rep);
 void dd_batch_destroy(dd_batch batch);
+
+/* ---- Continuous streams (Section III-A's input of t samples, chunk by chunk)
+ * A stream dedisperses a long observation in chunks of n_out samples per
+ * channel with the plan's delays. Each push takes the next chunk d_chunk
+ * [B][C][n_out] (rows of exactly n_out samples, the plan's input type) and
+ * writes d_out [B][D][n_out]: output samples [k*n_out - M, (k+1)*n_out - M) of
+ * the continuous stream, k = pushes so far, M = dd_stream_latency(s) = the
+ * plan's largest delay; input samples before the stream's start count as
+ * zero. The stream owns two device buffers of the plan's input shape and
+ * keeps the last M input samples between pushes; pushes on one stream must be
+ * ordered (same CUDA stream). The plan must outlive the stream. */
+dd_status dd_stream_create(dd_stream *out, dd_plan plan);
+dd_status dd_stream_push(dd_stream s, const void *d_chunk, const void *d_w, void *d_out,
+                         void *stream);
+dd_status dd_stream_reset(dd_stream s, void *stream);  /* back to an all-zero history */
+int64_t dd_stream_latency(dd_stream s);
+void dd_stream_destroy(dd_stream s);
 
 /* ---- Diagnostics ---------------------------------------------------------- */
 /* Failure-path check: enqueues one CTA that waits on a shared-memory

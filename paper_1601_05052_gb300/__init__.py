@@ -17,7 +17,7 @@ import torch
 from . import _lib
 from ._lib import DDError, DTYPES, Variant, TuneReport  # noqa: F401
 
-__all__ = ["Plan", "Batch", "dedisperse", "compute_shifts", "DDError", "variants"]
+__all__ = ["Plan", "Batch", "Stream", "dedisperse", "compute_shifts", "DDError", "variants"]
 
 _TORCH_DT = {"f32": torch.float32, "f16": torch.float16, "bf16": torch.bfloat16,
              "u8": torch.uint8}
@@ -270,3 +270,45 @@ class Batch:
             self._h, A(*[x.data_ptr() for x in xs]), A(*[w.data_ptr() for w in ws]),
             A(*[o.data_ptr() for o in outs]), _stream(stream)))
         return outs
+
+
+class Stream:
+    """Continuous dedispersion in chunks of `plan.n_out` samples per channel.
+
+    push(chunk [B][C][n_out]) returns the output samples
+    [k*n_out - latency, (k+1)*n_out - latency) of the continuous stream."""
+
+    def __init__(self, plan):
+        self.plan = plan
+        h = ctypes.c_void_p()
+        _lib.check(_lib_().dd_stream_create(ctypes.byref(h), plan._h))
+        self._h = h
+        self.latency = _lib_().dd_stream_latency(h)
+
+    def close(self):
+        if getattr(self, "_h", None):
+            _lib_().dd_stream_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def reset(self, stream=None):
+        _lib.check(_lib_().dd_stream_reset(self._h, _stream(stream)))
+
+    def push(self, chunk, w, out=None, stream=None):
+        p = self.plan
+        shape = (p.batch, p.n_chan, p.n_out)
+        if (tuple(chunk.shape) != shape or chunk.dtype != p.torch_dtype or not chunk.is_cuda
+                or not chunk.is_contiguous()):
+            raise ValueError("chunk must be a contiguous CUDA %s %s" % (shape, p.torch_dtype))
+        if tuple(w.shape) != (p.n_chan,) or w.dtype != p.w_dtype or not w.is_cuda:
+            raise ValueError("weights must be CUDA [%d] %s" % (p.n_chan, p.w_dtype))
+        if out is None:
+            out = torch.empty(p.out_shape, dtype=p.out_dtype, device=chunk.device)
+        _lib.check(_lib_().dd_stream_push(self._h, _ptr(chunk), _ptr(w), _ptr(out),
+                                          _stream(stream)))
+        return out

@@ -78,6 +78,11 @@ SIGNATURES = [
     ("dd_batch_set_variant", i32, [P, ctypes.POINTER(Variant)]),
     ("dd_batch_tune", i32, [P, i32, ctypes.POINTER(TuneReport)]),
     ("dd_batch_destroy", None, [P]),
+    ("dd_stream_create", i32, [ctypes.POINTER(P), P]),
+    ("dd_stream_push", i32, [P, P, P, P, P]),
+    ("dd_stream_reset", i32, [P, P]),
+    ("dd_stream_latency", i64, [P]),
+    ("dd_stream_destroy", None, [P]),
     ("dd_plan_check_device", i32, [P]),
     ("dd_status_str", ctypes.c_char_p, [i32]),
     ("dd_get_last_error", i32, []),

@@ -127,6 +127,11 @@ dd_status launch_adjoint(dd_plan_s *p, const float *g, const float *w, const flo
 
 bool aligned16(const void *p);
 
+// Tuning cache (DD_TUNE_CACHE): signature of a plan and a record of its
+// tuned variant.
+std::string plan_signature(const dd_plan_s *p);
+void cache_store(const std::string &key, const dd_variant &v);
+
 // Two-pass sweep of the variant grid (dd_tune.cpp). time_ms(v, &ms) sets ms
 // <= 0 for variants that do not fit; returns the fastest in *best.
 dd_status sweep_variants(int32_t budget_ms, double flop,

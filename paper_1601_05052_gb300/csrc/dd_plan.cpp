@@ -4,8 +4,11 @@
 #include <algorithm>
 #include <cmath>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
+#include <fstream>
 #include <limits>
+#include <sstream>
 
 #include "dd_internal.h"
 
@@ -266,6 +269,62 @@ const dd_variant kDefaults[] = {
     {0, 4, 4, 4, 2, 4, 2},  {0, 2, 4, 4, 2, 4, 2},  {0, 4, 2, 4, 1, 4, 2},
 };
 
+}  // namespace
+
+// ---- tuning cache: lines "<key> kind dpt spt warps_dm warps_time cch stages"
+// in the file named by DD_TUNE_CACHE; the key is the device name, input type,
+// shape and a hash of the delay table, so a tuned variant is reused only for
+// the same problem on the same kind of GPU.
+std::string plan_signature(const dd_plan_s *p) {
+    cudaDeviceProp prop{};
+    std::string dev = "unknown";
+    if (cudaGetDeviceProperties(&prop, p->device) == cudaSuccess) dev = prop.name;
+    for (char &ch : dev)
+        if (ch == ' ') ch = '_';
+    uint64_t h = 1469598103934665603ull;  // FNV-1a over the delay table
+    for (int32_t v : p->shifts) {
+        for (int i = 0; i < 4; ++i) {
+            h ^= uint64_t((uint32_t(v) >> (8 * i)) & 0xffu);
+            h *= 1099511628211ull;
+        }
+    }
+    std::ostringstream os;
+    os << dev << "/t" << int(p->dtype) << "/C" << p->C << "/D" << p->D << "/S" << p->S << "/B"
+       << p->B << "/" << std::hex << h;
+    return os.str();
+}
+
+bool cache_lookup(const std::string &key, dd_variant *v) {
+    const char *path = std::getenv("DD_TUNE_CACHE");
+    if (!path || !*path) return false;
+    std::ifstream f(path);
+    std::string line;
+    bool found = false;
+    while (std::getline(f, line)) {  // the last entry for a key wins
+        std::istringstream is(line);
+        std::string k;
+        dd_variant t{};
+        if (is >> k >> t.kind >> t.dm_per_thread >> t.samples_per_thread >> t.warps_dm >>
+            t.warps_time >> t.chans_per_stage >> t.stages) {
+            if (k == key) {
+                *v = t;
+                found = true;
+            }
+        }
+    }
+    return found;
+}
+
+void cache_store(const std::string &key, const dd_variant &v) {
+    const char *path = std::getenv("DD_TUNE_CACHE");
+    if (!path || !*path) return;
+    std::ofstream f(path, std::ios::app);
+    f << key << " " << v.kind << " " << v.dm_per_thread << " " << v.samples_per_thread << " "
+      << v.warps_dm << " " << v.warps_time << " " << v.chans_per_stage << " " << v.stages << "\n";
+}
+
+namespace {
+
 dd_status finish_plan(dd_plan_s *p, dd_plan *out) {
     p->max_shift = 0;
     for (int32_t s : p->shifts) p->max_shift = std::max(p->max_shift, s);
@@ -292,10 +351,11 @@ dd_status finish_plan(dd_plan_s *p, dd_plan *out) {
     if (e != cudaSuccess) return cuda_fail(e, "cudaMemset(err)");
 
     dd_status s = DD_ERR_UNSUPPORTED;
-    for (const dd_variant &dv : kDefaults) {
-        s = build_fwd_tables(p, dv, &p->fwd);
-        if (s == DD_OK) break;
-        if (s != DD_ERR_ARG) return s;
+    dd_variant cached{};
+    if (cache_lookup(plan_signature(p), &cached)) s = build_fwd_tables(p, cached, &p->fwd);
+    for (size_t i = 0; s != DD_OK && i < sizeof(kDefaults) / sizeof(kDefaults[0]); ++i) {
+        s = build_fwd_tables(p, kDefaults[i], &p->fwd);
+        if (s != DD_OK && s != DD_ERR_ARG) return s;
     }
     if (s != DD_OK)
         return fail(DD_ERR_UNSUPPORTED, "no forward variant fits this plan (delay spans too wide)");

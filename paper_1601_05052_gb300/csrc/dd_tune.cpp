@@ -157,5 +157,6 @@ extern "C" dd_status dd_tune(dd_plan p, int32_t budget_ms, dd_tune_report *rep) 
     if (s != DD_OK) return s;
     free_fwd_tables(&p->fwd);
     p->fwd = t;
+    cache_store(plan_signature(p), best);
     return DD_OK;
 }

@@ -153,6 +153,44 @@ def test_tuned_variant_stays_correct():
     check_full(plan, x, w, sh, "f32", "tuned")
 
 
+def test_tuning_cache_restores_the_tuned_variant(tmp_path, monkeypatch):
+    """dd_tune records its winner under DD_TUNE_CACHE; a new plan of the same
+    problem starts from it, a plan of another problem does not."""
+    cache = tmp_path / "tune.txt"
+    monkeypatch.setenv("DD_TUNE_CACHE", str(cache))
+    rng = np.random.default_rng(11)
+    sh, x, w = random_case(rng, 1, 64, 48, 2000, 300, "f32")
+    plan = Plan(shifts=sh, n_out=2000, batch=1)
+    default = plan.variant
+    rep = plan.tune(budget_ms=2000)
+    assert cache.read_text().count("\n") == 1
+    # force a non-default winner into the cache so that the restore is visible
+    other = next(v for v in variants() if v["kind"] == 0 and v != default
+                 and _fits(sh, 2000, v))
+    line = cache.read_text().split()[0]
+    cache.write_text(cache.read_text() + "%s %d %d %d %d %d %d %d\n" % (
+        line, other["kind"], other["dm_per_thread"], other["samples_per_thread"],
+        other["warps_dm"], other["warps_time"], other["chans_per_stage"], other["stages"]))
+    again = Plan(shifts=sh, n_out=2000, batch=1)
+    assert again.variant == other
+    check_full(again, x, w, sh, "f32", "cached")
+    sh2 = sh.copy()
+    sh2[0, 0] += 1
+    assert Plan(shifts=sh2, n_out=2000, batch=1).variant == default
+    assert rep["best"] == plan.variant
+    monkeypatch.delenv("DD_TUNE_CACHE")
+    assert Plan(shifts=sh, n_out=2000, batch=1).variant == default
+
+
+def _fits(sh, n_out, v):
+    p = Plan(shifts=sh, n_out=n_out, batch=1)
+    try:
+        p.variant = v
+        return True
+    except Exception:
+        return False
+
+
 def test_survey_scale_f32_sampled():
     """The benchmark workload (1024 ch, 2048 trials, 20000 samples, FP32) in
     the launch configuration the benchmark times: sampled outputs, plus the
@@ -198,3 +236,37 @@ def test_bounded_wait_reports_timeout_and_context_survives():
     assert e.value.status == 5  # DD_ERR_TIMEOUT
     plan.check_device()  # the error word was cleared
     check_full(plan, x, w, sh, "f32", "after timeout")
+
+
+@pytest.mark.parametrize("dtype", ["f32", "u8"])
+def test_stream_equals_one_long_dedispersion(dtype):
+    """Pushing K chunks through a stream gives the dedispersion of the whole
+    concatenated input with M leading zeros, output delayed by M samples."""
+    from paper_1601_05052_gb300 import Stream
+    rng = np.random.default_rng(31)
+    C, D, S, K, M = 13, 11, 160, 5, 400
+    sh = np.sort(rng.integers(0, M + 1, size=(D, C)), axis=0)
+    sh[-1, 0] = M
+    plan = Plan(shifts=sh, n_out=S, batch=2, dtype=dtype)
+    st = Stream(plan)
+    assert st.latency == M
+    xf = rng.standard_normal((2, C, K * S)).astype(np.float32)
+    x = xf if dtype == "f32" else synth.quantize_u8(xf)
+    w = rng.uniform(0.5, 1.5, C).astype(np.float32)
+    if dtype == "u8":
+        w = synth.quantize_weights_q8(w)
+    wd = weights_dev(w, dtype)
+    outs = [st.push(to_dev(np.ascontiguousarray(x[:, :, k * S:(k + 1) * S]), dtype), wd).cpu().numpy()
+            for k in range(K)]
+    got = np.concatenate(outs, axis=2)
+    full = np.zeros((2, C, M + K * S + 16), dtype=x.dtype)
+    full[:, :, M:M + K * S] = x
+    if dtype == "u8":
+        ref = oracle.forward_u8(full, w, sh, K * S)
+        np.testing.assert_array_equal(got.astype(np.int64), ref)
+    else:
+        ref, ab = oracle.forward(full, w, sh, K * S, with_absum=True)
+        assert_float_parity(got, ref, ab, what="stream")
+    st.reset()
+    again = st.push(to_dev(np.ascontiguousarray(x[:, :, :S]), dtype), wd).cpu().numpy()
+    np.testing.assert_array_equal(again, outs[0])
