@@ -43,7 +43,8 @@ METRIC = "DM-trial·samples/s"
 KERNEL_SOURCES = ["paper_1601_05052_gb300/csrc/dd_fwd_tile.cuh",
                   "paper_1601_05052_gb300/csrc/dd_fwd.cu",
                   "paper_1601_05052_gb300/csrc/dd_ptx.cuh",
-                  "paper_1601_05052_gb300/csrc/dd_plan.cpp"]
+                  "paper_1601_05052_gb300/csrc/dd_plan.cpp",
+                  "paper_1601_05052_gb300/csrc/dd_kinds.h"]
 TRAFFIC_PROFILE = "profiles/fwd_survey_f32.md"
 UNIT = "DM-trial·samples/s"
 WORKLOAD = "cfg2"

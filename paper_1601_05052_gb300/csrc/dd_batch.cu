@@ -33,8 +33,7 @@ struct BatchArgs {
 };
 
 template <int KIND, typename T, int DPT, int SPT>
-__global__ void __launch_bounds__(KIND == 3 ? 384 : (KIND == 2 ? 288 : 256),
-                      KIND == 2 ? (DPT * SPT <= 16 ? 3 : 2) : (KIND == 3 ? 2 : 1))
+__global__ void __launch_bounds__(fwd_max_threads(KIND), fwd_min_blocks(KIND, DPT, SPT))
     dd_fwd_persistent_kernel(const BatchArgs ba) {
     extern __shared__ __align__(128) unsigned char smem[];
     __shared__ long long s_item;
@@ -191,6 +190,7 @@ dd_status configure(dd_batch_s *bt, const dd_variant &v) {
         a.desc = t.d_desc;
         a.offs = t.d_offs;
         a.bdesc = t.d_bdesc;
+        a.n_blocks = t.n_blocks;
         a.p_elems = t.p_elems;
         a.err = p->d_err;
         bt->ba.item_start[i] = acc;

@@ -13,8 +13,7 @@
 namespace dd {
 
 template <int KIND, typename T, int DPT, int SPT>
-__global__ void __launch_bounds__(KIND == 3 ? 384 : (KIND == 2 ? 288 : 256),
-                      KIND == 2 ? (DPT * SPT <= 16 ? 3 : 2) : (KIND == 3 ? 2 : 1))
+__global__ void __launch_bounds__(fwd_max_threads(KIND), fwd_min_blocks(KIND, DPT, SPT))
     dd_fwd_kernel(const FwdArgs a) {
     extern __shared__ __align__(128) unsigned char smem[];
     uint64_t *bars = reinterpret_cast<uint64_t *>(smem);
@@ -136,6 +135,7 @@ dd_status launch_forward(dd_plan_s *p, const FwdTables &t, const void *in, const
     a.desc = t.d_desc;
     a.offs = t.d_offs;
     a.bdesc = t.d_bdesc;
+    a.n_blocks = t.n_blocks;
     a.p_elems = t.p_elems;
     a.err = p->d_err;
     dim3 grid(unsigned(t.n_dtiles), unsigned(t.n_ttiles), unsigned(p->B));

@@ -31,6 +31,8 @@
 //    partial value per group instead of one input value per channel (the
 //    same sums, associated per group). A dedicated producer warp stages the
 //    chunks; the compute warps meet at one named barrier per chunk.
+//  kind 4, wide sub-band: kind 2 in CTAs of up to 16 trial warps (one
+//    resident CTA per SM), for DM tiles of 128 trials.
 //  kind 3, warp-specialised sub-band: kind 2's arithmetic with 4 extra
 //    builder warps; mbarriers on the staging slots and on 3 partial-sum
 //    slots replace every CTA-wide barrier.
@@ -41,12 +43,15 @@
 #include <cstdint>
 #include <type_traits>
 
+#include "dd_kinds.h"
 #include "dd_ptx.cuh"
 
 // The compiled forward kernels: X(kind, dm_per_thread, samples_per_thread).
+// Kind 4 is kind 2 in CTAs of up to 16 trial warps (one CTA per SM), so a
+// DM tile can span 128 trials and amortise each partial series over more of them.
 #define DD_FWD_KEYS(X)                                                                    \
     X(0, 2, 4) X(0, 4, 2) X(0, 4, 4) X(0, 8, 2) X(0, 8, 4) X(0, 4, 8) X(1, 8, 9) X(2, 4, 4) \
-        X(2, 4, 8) X(2, 8, 4) X(2, 8, 2) X(3, 8, 4) X(3, 4, 8) X(3, 8, 2)
+        X(2, 4, 8) X(2, 8, 4) X(2, 8, 2) X(3, 8, 4) X(3, 4, 8) X(3, 8, 2) X(4, 8, 4) X(4, 4, 8)
 
 namespace dd {
 
@@ -56,13 +61,10 @@ constexpr int kRwRmax = 15;
 // warps and partial-sum slots of kind 3.
 constexpr int kSbG = 4;
 constexpr int kSbP = 8;
-constexpr int kWsBuilders = 4;
 constexpr int kWsPSlots = 3;
-
-// Warps a CTA has beyond its warps_dm * warps_time trial warps.
-__host__ __device__ constexpr int extra_warps(int kind) {
-    return kind == 3 ? kWsBuilders : (kind == 2 ? 1 : 0);
-}
+// Chunks whose channel descriptors a producer warp holds in registers ahead
+// of issuing their copies.
+constexpr int kDescAhead = 4;
 
 template <typename T>
 struct Elem;
@@ -103,8 +105,9 @@ struct FwdArgs {
     int n_dtiles, n_ttiles, B;
     const int4 *desc;
     const uint16_t *offs;
-    const int4 *bdesc;  // kinds 2 and 3
-    int p_elems;        // kinds 2 and 3
+    const int4 *bdesc;  // sub-band kinds: build blocks [n_dtiles][n_chunks][n_blocks]
+    int n_blocks;       // sub-band kinds
+    int p_elems;        // sub-band kinds
     int *err;
 };
 
@@ -134,6 +137,12 @@ __device__ __forceinline__ void load_offsets(const uint16_t *p, int (&o)[DPT]) {
     }
 }
 
+// Barrier over the first n threads of the CTA (named barrier 1): the
+// compute warps of a kind-2 CTA synchronise without the producer warp.
+__device__ __forceinline__ void compute_barrier(int n) {
+    asm volatile("bar.sync 1, %0;" ::"r"(n) : "memory");
+}
+
 // Packed FP32 pair arithmetic of sm_100-class GPUs (one instruction for two
 // lanes' worth of adds / fmas): a += b and d = a * b + c element-wise.
 __device__ __forceinline__ void add2(float &a0, float &a1, float b0, float b1) {
@@ -159,8 +168,8 @@ struct Stager {
     const T *in_b;
     long long t0;
     const int4 *desc_k;
-    const void *tab_k;    // kind 0/1: trial offsets; kind 2/3: group offsets
-    const int4 *bdesc_k;  // kind 2/3 only
+    const void *tab_k;    // kind 0/1: trial offsets; sub-band kinds: group offsets
+    const int4 *bdesc_k;  // sub-band kinds: this DM tile's build blocks
     uint32_t tab_bytes;   // per chunk, both tables
     uint32_t tab1_bytes;  // per chunk, first table
     unsigned char *stage0;
@@ -204,7 +213,7 @@ struct Stager {
                 const int g0i = c0 / kSbG;
                 bulk_g2s(tb, static_cast<const uint16_t *>(tab_k) + (size_t)g0i * a.Dt,
                          tab1_bytes, full);
-                bulk_g2s(tb + tab1_bytes, bdesc_k + (size_t)g0i * kSbP * 2, tab_bytes - tab1_bytes,
+                bulk_g2s(tb + tab1_bytes, bdesc_k + (size_t)k * a.n_blocks, tab_bytes - tab1_bytes,
                          full);
             }
             // the chunk's weights; a 16-byte granule never crosses a page, so
@@ -225,8 +234,9 @@ __device__ __forceinline__ Stager<T> make_stager(const FwdArgs &a, int dtile, in
                 a.desc + (size_t)dtile * a.C_pad,
                 subband ? static_cast<const void *>(a.offs + (size_t)dtile * g_pad * a.Dt)
                         : static_cast<const void *>(a.offs + (size_t)dtile * a.C_pad * a.Dt),
-                subband ? a.bdesc + (size_t)dtile * g_pad * kSbP * 2 : nullptr,
-                subband ? uint32_t(gpc) * a.Dt * 2 + uint32_t(gpc) * kSbP * 32
+                subband ? a.bdesc + (size_t)dtile * ((a.C + a.cch - 1) / a.cch) * a.n_blocks
+                        : nullptr,
+                subband ? uint32_t(gpc) * a.Dt * 2 + uint32_t(a.n_blocks) * 16
                         : uint32_t(a.cch) * a.Dt * 2,
                 subband ? uint32_t(gpc) * a.Dt * 2 : uint32_t(a.cch) * a.Dt * 2,
                 stage0,
@@ -340,11 +350,12 @@ template <int KIND>
 __device__ __forceinline__ void fwd_init_barriers(uint64_t *bars, int stages) {
     if (threadIdx.x == 0) {
         const int n_warps = int(blockDim.x >> 5);
-        const int releasers = KIND == 3 ? kWsBuilders : (KIND == 2 ? 1 : n_warps);
+        const int releasers = KIND == 3 ? kWsBuilders : ((KIND == 2 || KIND == 4) ? 1 : n_warps);
         for (int s = 0; s < stages; ++s) {
             mbar_init(&bars[s], 1);
             mbar_init(&bars[8 + s], uint32_t(releasers));
         }
+        *reinterpret_cast<volatile int *>(&bars[7]) = 0;  // the CTA's give-up flag
         if (KIND == 3) {
             for (int q = 0; q < kWsPSlots; ++q) {
                 mbar_init(&bars[4 + q], uint32_t(kWsBuilders));
@@ -439,96 +450,114 @@ __device__ __forceinline__ void fwd_tile(const FwdArgs &a, int dtile, int ttile,
 
 // ------------------------------------------------------------------ kinds 2 and 3
 
-// Builds part of one partial series: dst[u] = sum_{j<gn} wg[j] * raw[r[j] + u]
-// for u in [u0, u1), lanes of a warp striding by 32 and each lane keeping 4
-// elements in flight so the shared-memory loads overlap.
+// Builds this worker's share of a chunk's partial series from the chunk's
+// build blocks. A block covers up to 4 sub-blocks of 32 consecutive
+// elements of one series: {dst, r0, (r1-r0) | (r2-r0) << 16, (r3-r0) |
+// group << 16 | channels << 20 | sub-blocks << 24}, and lane l of sub-block s
+// writes P[dst + 32 s + l] = sum_{j < channels} w[4 group + j] *
+// raw[r_j + 32 s + l]. Worker `part` of `parts` takes blocks part, part +
+// parts, ...; the next block's descriptor is loaded while the current one is
+// built, and all of a block's operand loads are issued before its
+// arithmetic. Blocks with 0 sub-blocks are capacity padding.
 template <typename T>
-__device__ __forceinline__ void sb_build(typename Elem<T>::Acc *dst, const T *raw,
-                                         const int (&r)[4], const typename Elem<T>::W (&wg)[4],
-                                         int gn, int u0, int u1, int lane) {
+__device__ __forceinline__ void sb_build_blocks(typename Elem<T>::Acc *P, const T *raw,
+                                                const int4 *blk, const typename Elem<T>::W *sw,
+                                                int n_blocks, int part, int parts, int lane) {
     using Acc = typename Elem<T>::Acc;
-    if (gn == kSbG) {
-        const T *r0 = raw + r[0], *r1 = raw + r[1], *r2 = raw + r[2], *r3 = raw + r[3];
-        int u = u0 + lane;
-        for (; u + 96 < u1; u += 128) {
-            Acc v[4];
-            if constexpr (std::is_same<Acc, float>::value) {
+    using Wt = typename Elem<T>::W;
+    static_assert(sizeof(Wt) == 4, "weights are 4-byte words");
+    int b = part;
+    int4 d = b < n_blocks ? blk[b] : make_int4(0, 0, 0, 0);
+    while (b < n_blocks) {
+        const int bn = b + parts;
+        const int4 dn = bn < n_blocks ? blk[bn] : make_int4(0, 0, 0, 0);
+        const int nsub = (d.w >> 24) & 7;
+        if (nsub) {
+            const int g = (d.w >> 16) & 3, gn = (d.w >> 20) & 7;
+            const int4 wv = *reinterpret_cast<const int4 *>(sw + 4 * g);
+            const Wt w[4] = {__builtin_bit_cast(Wt, wv.x), __builtin_bit_cast(Wt, wv.y),
+                             __builtin_bit_cast(Wt, wv.z), __builtin_bit_cast(Wt, wv.w)};
+            const int r0 = d.y + lane;
+            const int r[4] = {r0, r0 + int(short(d.z & 0xffff)), r0 + (d.z >> 16),
+                              r0 + int(short(d.w & 0xffff))};
+            Acc x[4][4];  // [sub-block][channel]
 #pragma unroll
-                for (int q = 0; q < 4; q += 2) {  // two elements per packed instruction
-                    const int x = u + 32 * q, y = x + 32;
-                    v[q] = wg[0] * Elem<T>::val(r0[x]);
-                    v[q + 1] = wg[0] * Elem<T>::val(r0[y]);
-                    fma2(v[q], v[q + 1], wg[1], wg[1], Elem<T>::val(r1[x]), Elem<T>::val(r1[y]));
-                    fma2(v[q], v[q + 1], wg[2], wg[2], Elem<T>::val(r2[x]), Elem<T>::val(r2[y]));
-                    fma2(v[q], v[q + 1], wg[3], wg[3], Elem<T>::val(r3[x]), Elem<T>::val(r3[y]));
+            for (int q = 0; q < 4; ++q)
+                if (q < nsub) {
+#pragma unroll
+                    for (int j = 0; j < 4; ++j) x[q][j] = Elem<T>::val(raw[r[j] + 32 * q]);
                 }
-            } else {
+            Acc v[4];
+            if (gn == kSbG) {
+                if constexpr (std::is_same<Acc, float>::value) {
+#pragma unroll
+                    for (int q = 0; q < 4; q += 2) {
+                        v[q] = w[0] * x[q][0];
+                        v[q + 1] = w[0] * x[q + 1][0];
+#pragma unroll
+                        for (int j = 1; j < 4; ++j)
+                            fma2(v[q], v[q + 1], w[j], w[j], x[q][j], x[q + 1][j]);
+                    }
+                } else {
+#pragma unroll
+                    for (int q = 0; q < 4; ++q)
+                        v[q] = w[0] * x[q][0] + w[1] * x[q][1] + w[2] * x[q][2] + w[3] * x[q][3];
+                }
+            } else {  // the last group of a plan may hold fewer channels
 #pragma unroll
                 for (int q = 0; q < 4; ++q) {
-                    const int x = u + 32 * q;
-                    v[q] = wg[0] * Elem<T>::val(r0[x]) + wg[1] * Elem<T>::val(r1[x]) +
-                           wg[2] * Elem<T>::val(r2[x]) + wg[3] * Elem<T>::val(r3[x]);
+                    v[q] = w[0] * x[q][0];
+#pragma unroll
+                    for (int j = 1; j < kSbG; ++j)
+                        if (j < gn) v[q] += w[j] * x[q][j];
                 }
             }
 #pragma unroll
-            for (int q = 0; q < 4; ++q) dst[u + 32 * q] = v[q];
+            for (int q = 0; q < 4; ++q)
+                if (q < nsub) P[d.x + 32 * q + lane] = v[q];
         }
-        for (; u < u1; u += 32)
-            dst[u] = wg[0] * Elem<T>::val(r0[u]) + wg[1] * Elem<T>::val(r1[u]) +
-                     wg[2] * Elem<T>::val(r2[u]) + wg[3] * Elem<T>::val(r3[u]);
-    } else {  // the last group of a plan may hold fewer channels
-        for (int u = u0 + lane; u < u1; u += 32) {
-            Acc v = wg[0] * Elem<T>::val(raw[r[0] + u]);
-#pragma unroll
-            for (int j = 1; j < kSbG; ++j)
-                if (j < gn) v += wg[j] * Elem<T>::val(raw[r[j] + u]);
-            dst[u] = v;
-        }
+        d = dn;
+        b = bn;
     }
 }
 
-// Builds this warp's share of a chunk's partial series. The chunk's valid
-// build entries are compacted at its head and laid out back to back in the
-// partial-sum buffer, so the buffer's E elements are split evenly: worker
-// `part` of `parts` builds elements [E*part/parts, E*(part+1)/parts), touching
-// the one to few entries that overlap that range (found with one ballot).
-template <typename T>
-__device__ __forceinline__ void sb_build_share(typename Elem<T>::Acc *P, const T *raw,
-                                               const int4 *bd, const typename Elem<T>::W *sw,
-                                               int n_slots, int part, int parts, int lane) {
-    using Wt = typename Elem<T>::W;
-    int4 A = make_int4(0, 0, 0, 0);
-    if (lane < n_slots) A = bd[2 * lane];
-    int end = A.x + A.y;  // entries are in buffer order: the last valid one ends at E
-#pragma unroll
-    for (int m = 16; m >= 1; m >>= 1) end = max(end, __shfl_xor_sync(0xffffffffu, end, m));
-    const int E = end;
-    const int i0 = int((long long)E * part / parts), i1 = int((long long)E * (part + 1) / parts);
-    unsigned mask = __ballot_sync(0xffffffffu, A.y > 0 && A.x < i1 && A.x + A.y > i0);
-    while (mask) {
-        const int e = __ffs(mask) - 1;
-        mask &= mask - 1;
-        const int4 Ae = bd[2 * e];
-        const int4 Be = bd[2 * e + 1];
-        const int gn = Be.z, g = Be.w;
-        Wt wg[4];
-#pragma unroll
-        for (int j = 0; j < 4; ++j) wg[j] = j < gn ? sw[g * kSbG + j] : Wt(0);
-        const int r[4] = {Ae.z, Ae.w, Be.x, Be.y};
-        const int u0 = max(i0, Ae.x) - Ae.x, u1 = min(i1, Ae.x + Ae.y) - Ae.x;
-        sb_build<T>(P + Ae.x, raw, r, wg, gn, u0, u1, lane);
+// The packed 16-bit offsets of all the chunk's groups are loaded first, so
+// their shared-memory latency is paid once per chunk rather than per group.
+template <int DPT>
+struct OffWords {
+    uint32_t w[DPT / 2];
+};
+template <int DPT>
+__device__ __forceinline__ OffWords<DPT> load_offwords(const uint16_t *p) {
+    OffWords<DPT> r;
+    if constexpr (DPT == 8) {
+        const uint4 v = *reinterpret_cast<const uint4 *>(p);
+        r.w[0] = v.x, r.w[1] = v.y, r.w[2] = v.z, r.w[3] = v.w;
+    } else if constexpr (DPT == 4) {
+        const uint2 v = *reinterpret_cast<const uint2 *>(p);
+        r.w[0] = v.x, r.w[1] = v.y;
+    } else {
+        r.w[0] = *reinterpret_cast<const uint32_t *>(p);
     }
+    return r;
 }
 
-// The trial loop of a sub-band chunk: one partial value per group per output.
 template <typename Acc, int DPT, int SPT>
 __device__ __forceinline__ void sb_trials(Acc (&acc)[DPT][SPT], const Acc *Pl,
                                           const uint16_t *poffs, int Dt, int ng) {
+    OffWords<DPT> ow[4];
+#pragma unroll
+    for (int g = 0; g < 4; ++g)
+        if (g < ng) ow[g] = load_offwords<DPT>(poffs + g * Dt);
 #pragma unroll
     for (int g = 0; g < 4; ++g) {  // at most 16 channels = 4 groups per chunk
         if (g < ng) {
             int o[DPT];
-            load_offsets<DPT>(poffs + g * Dt, o);
+#pragma unroll
+            for (int i = 0; i < DPT / 2; ++i) {
+                o[2 * i] = int(ow[g].w[i] & 0xffffu);
+                o[2 * i + 1] = int(ow[g].w[i] >> 16);
+            }
 #pragma unroll
             for (int i = 0; i < DPT; ++i) {
                 const Acc *src = Pl + o[i];
@@ -545,12 +574,6 @@ __device__ __forceinline__ void sb_trials(Acc (&acc)[DPT][SPT], const Acc *Pl,
     }
 }
 
-// Barrier over the first n threads of the CTA (named barrier 1): the
-// compute warps of a kind-2 CTA synchronise without the producer warp.
-__device__ __forceinline__ void compute_barrier(int n) {
-    asm volatile("bar.sync 1, %0;" ::"r"(n) : "memory");
-}
-
 // kind 2: sub-band partial sums with a producer warp. Warps [0, NC) compute;
 // warp NC only stages chunks, running up to `stages` chunks ahead and
 // throttled by the slots' empty barriers (one arrival per chunk, made after
@@ -558,7 +581,9 @@ __device__ __forceinline__ void compute_barrier(int n) {
 // partial series (and copy the chunk's trial offsets next to them), meet at
 // a named barrier, release the staging slot and run the trial loop.
 // Partial-sum slots alternate by global chunk parity, so a chunk's build
-// never overwrites what slower warps still read.
+// never overwrites what slower warps still read. (Replacing the barrier by
+// per-warp mbarrier hand-offs, so that a warp builds chunk k+1 before its
+// trials on chunk k, measured slower on GB300.)
 template <typename T, int DPT, int SPT>
 __device__ __forceinline__ void fwd_tile_sb(const FwdArgs &a, int dtile, int ttile, int b,
                                             uint64_t *bars, unsigned char *stage0,
@@ -566,6 +591,7 @@ __device__ __forceinline__ void fwd_tile_sb(const FwdArgs &a, int dtile, int tti
     using Acc = typename Elem<T>::Acc;
     using Wt = typename Elem<T>::W;
     uint64_t *full = bars, *empty = bars + 8;
+    volatile int *gave_up = reinterpret_cast<volatile int *>(&bars[7]);
     const uint32_t S = uint32_t(a.stages);
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int nc = int(blockDim.x >> 5) - 1;  // compute warps; warp nc produces
@@ -578,14 +604,33 @@ __device__ __forceinline__ void fwd_tile_sb(const FwdArgs &a, int dtile, int tti
 
     if (warp == nc) {
         // ---------------- producer warp
-        int4 dsc = st.desc(0, lane);
-        for (int k = 0; k < n_chunks; ++k) {
-            const uint32_t kg = kbase + uint32_t(k);
-            const int slot = int(kg % S);
-            const int4 next = (k + 1 < n_chunks) ? st.desc(k + 1, lane) : make_int4(0, 0, 0, 0);
-            if (kg >= S) mbar_wait_bounded(&empty[slot], ((kg / S) - 1u) & 1u, a.err);
-            st.issue(k, slot, dsc, &full[slot], lane);
-            dsc = next;
+        // Channel descriptors are loaded kDescAhead chunks before their copy
+        // is issued, so the issue rate is not bound by one global-memory
+        // latency per chunk.
+        // The ring is indexed by compile-time positions (the loop over j is
+        // unrolled), so a descriptor is loaded into the register it is
+        // consumed from kDescAhead chunks later, with no move that would wait
+        // for the load.
+        int4 q[kDescAhead];
+#pragma unroll
+        for (int j = 0; j < kDescAhead; ++j)
+            q[j] = j < n_chunks ? st.desc(j, lane) : make_int4(0, 0, 0, 0);
+        for (int k0 = 0; k0 < n_chunks; k0 += kDescAhead) {
+#pragma unroll
+            for (int j = 0; j < kDescAhead; ++j) {
+                const int k = k0 + j;
+                if (k < n_chunks) {
+                    const uint32_t kg = kbase + uint32_t(k);
+                    const int slot = int(kg % S);
+                    bool ok = true;
+                    if (kg >= S)
+                        ok = mbar_wait_bounded(&empty[slot], ((kg / S) - 1u) & 1u, a.err,
+                                               kWaitBudgetNs, gave_up);
+                    if (__all_sync(0xffffffffu, ok)) st.issue(k, slot, q[j], &full[slot], lane);
+                    q[j] = k + kDescAhead < n_chunks ? st.desc(k + kDescAhead, lane)
+                                                     : make_int4(0, 0, 0, 0);
+                }
+            }
         }
         kbase += uint32_t(n_chunks);
         return;
@@ -603,7 +648,11 @@ __device__ __forceinline__ void fwd_tile_sb(const FwdArgs &a, int dtile, int tti
     for (int k = 0; k < n_chunks; ++k) {
         const uint32_t kg = kbase + uint32_t(k);
         const int slot = int(kg % S);
-        mbar_wait_bounded(&full[slot], (kg / S) & 1u, a.err);
+        // A failed wait sets the give-up flag before the barrier; after it
+        // every warp sees the flag and skips the trials on the chunk.
+        const bool ok = __all_sync(
+            0xffffffffu,
+            mbar_wait_bounded(&full[slot], (kg / S) & 1u, a.err, kWaitBudgetNs, gave_up));
         const unsigned char *sb = stage0 + slot * st.stage_bytes;
         const T *raw = reinterpret_cast<const T *>(sb);
         const int4 *bd = reinterpret_cast<const int4 *>(sb + a.stage_data_bytes + poffs_bytes);
@@ -613,13 +662,15 @@ __device__ __forceinline__ void fwd_tile_sb(const FwdArgs &a, int dtile, int tti
         uint16_t *poffs = reinterpret_cast<uint16_t *>(pb + a.p_elems * int(sizeof(Acc)));
         const int ng = (min(a.cch, a.C - k * a.cch) + kSbG - 1) / kSbG;
 
-        sb_build_share<T>(P, raw, bd, sw, ng * kSbP, warp, nc, lane);
-        {  // the chunk's trial offsets move next to its partial sums
+        if (ok) {
+            sb_build_blocks<T>(P, raw, bd, sw, a.n_blocks, warp, nc, lane);
+            // the chunk's trial offsets move next to its partial sums
             const uint32_t *src = reinterpret_cast<const uint32_t *>(sb + a.stage_data_bytes);
             uint32_t *dst = reinterpret_cast<uint32_t *>(poffs);
             for (int i = tid; i < int(poffs_bytes / 4); i += nc * 32) dst[i] = src[i];
         }
         compute_barrier(nc * 32);
+        if (*gave_up) continue;  // no arrival: the producer's next wait fails too
         if (tid == 0) mbar_arrive(&empty[slot]);  // nothing reads this staging slot any more
         sb_trials<Acc, DPT, SPT>(acc, P + lb, poffs + wd * DPT, a.Dt, ng);
     }
@@ -677,9 +728,8 @@ __device__ __forceinline__ void fwd_tile_ws(const FwdArgs &a, int dtile, int tti
                 reinterpret_cast<const int4 *>(sb + a.stage_data_bytes + poffs_bytes);
             const Wt *sw = reinterpret_cast<const Wt *>(sb + a.stage_data_bytes + st.tab_bytes);
             unsigned char *pb = pslot0 + ps * pslot_bytes;
-            const int ng = (min(a.cch, a.C - k * a.cch) + kSbG - 1) / kSbG;
-            sb_build_share<T>(reinterpret_cast<Acc *>(pb), raw, bd, sw, ng * kSbP, bw, kWsBuilders,
-                              lane);
+            sb_build_blocks<T>(reinterpret_cast<Acc *>(pb), raw, bd, sw, a.n_blocks, bw,
+                               kWsBuilders, lane);
             if (bw == 0) {  // the trial offsets travel with the partial sums
                 const uint32_t *src = reinterpret_cast<const uint32_t *>(sb + a.stage_data_bytes);
                 uint32_t *dsto = reinterpret_cast<uint32_t *>(pb + a.p_elems * int(sizeof(Acc)));
@@ -726,7 +776,7 @@ template <int KIND, typename T, int DPT, int SPT>
 __device__ __forceinline__ void fwd_tile_any(const FwdArgs &a, int dtile, int ttile, int b,
                                              uint64_t *bars, unsigned char *stage0,
                                              uint32_t &kbase) {
-    if constexpr (KIND == 2)
+    if constexpr (KIND == 2 || KIND == 4)
         fwd_tile_sb<T, DPT, SPT>(a, dtile, ttile, b, bars, stage0, kbase);
     else if constexpr (KIND == 3)
         fwd_tile_ws<T, DPT, SPT>(a, dtile, ttile, b, bars, stage0, kbase);

@@ -12,6 +12,7 @@
 
 #include "../../include/dd.h"
 #include "dd_errbits.h"
+#include "dd_kinds.h"
 
 namespace dd {
 
@@ -45,11 +46,13 @@ struct FwdTables {
     size_t smem_bytes = 0;       // dynamic shared memory of one CTA
     int4 *d_desc = nullptr;
     uint16_t *d_offs = nullptr;
-    // kind 2 (sub-band) only: d_offs holds per-group trial offsets into the
-    // partial-sum buffer, [n_dtiles][C_pad/4][Dt]; d_bdesc the partial-series
-    // build descriptors, [n_dtiles][C_pad/4][kSbPatterns] x 2 int4; p_elems
-    // the partial-sum buffer length of one chunk.
+    // sub-band kinds only: d_offs holds per-group trial offsets into the
+    // partial-sum buffer, [n_dtiles][C_pad/4][Dt]; d_bdesc the build blocks
+    // of every chunk, [n_dtiles][n_chunks][n_blocks] int4 (one block = 32
+    // consecutive partial-series elements, see build_fwd_tables); p_elems the
+    // partial-sum buffer length of one chunk.
     int4 *d_bdesc = nullptr;
+    int n_blocks = 0;
     int p_elems = 0;
 };
 

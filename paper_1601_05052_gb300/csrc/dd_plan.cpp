@@ -43,8 +43,8 @@ bool aligned16(const void *p) { return (reinterpret_cast<uintptr_t>(p) & 15u) ==
 dd_status check_variant_shape(const dd_variant &v) {
     if (!fwd_variant_compiled(v.kind, v.dm_per_thread, v.samples_per_thread))
         return fail(DD_ERR_ARG, "variant (kind, dm_per_thread, samples_per_thread) not compiled");
-    if (v.warps_dm < 1 || v.warps_time < 1 || v.warps_dm * v.warps_time > 8)
-        return fail(DD_ERR_ARG, "variant warps_dm * warps_time must be in [1, 8]");
+    if (v.warps_dm < 1 || v.warps_time < 1 || v.warps_dm * v.warps_time > max_trial_warps(v.kind))
+        return fail(DD_ERR_ARG, "variant warps_dm * warps_time must be in [1, 8] (kind 4: [1, 16])");
     if (v.chans_per_stage != 4 && v.chans_per_stage != 8 && v.chans_per_stage != 16)
         return fail(DD_ERR_ARG, "variant chans_per_stage must be 4, 8 or 16");
     if (v.stages < 2 || v.stages > 4) return fail(DD_ERR_ARG, "variant stages must be 2..4");
@@ -99,6 +99,7 @@ dd_status sb_chunk(const dd_plan_s *p, int d0, int d1, int Dt, int Ts, int c0, i
         }
         std::vector<int64_t> pso(pats.size());
         for (size_t q = 0; q < pats.size(); ++q) {
+            // each series takes a whole number of 32-element build blocks
             const int64_t L = int64_t(bmax[q]) - bmin[q] + Ts;
             pso[q] = psoff;
             int *bd = &out->bdesc[(size_t(g) * kSbPatterns + q) * 8];
@@ -109,7 +110,7 @@ dd_status sb_chunk(const dd_plan_s *p, int d0, int d1, int Dt, int Ts, int c0, i
                 bd[2 + j] = int(r.z + bmin[q] + pats[q][size_t(j)] - r.x);
             }
             bd[6] = gn;
-            psoff += L;
+            psoff += round_up(L, 32);
         }
         for (int i = 0; i < Dt; ++i) {
             const int d = d0 + i;
@@ -138,7 +139,7 @@ dd_status build_fwd_tables(dd_plan_s *p, const dd_variant &v, FwdTables *out) {
     t.C_pad = (p->C + cch - 1) / cch * cch;
     const int al = align_elems(p->dtype);
     const int elt = elt_bytes(p->dtype);
-    const bool sb = v.kind == 2 || v.kind == 3;
+    const bool sb = is_subband(v.kind);
     if (t.n_ttiles > 65535) return fail(DD_ERR_ARG, "too many time tiles for this variant");
     if (sb && t.Dt % 8 != 0) return fail(DD_ERR_ARG, "sub-band variants need 8 | DM tile");
 
@@ -146,8 +147,10 @@ dd_status build_fwd_tables(dd_plan_s *p, const dd_variant &v, FwdTables *out) {
     std::vector<int4> desc(size_t(t.n_dtiles) * t.C_pad, make_int4(0, 0, 0, 0));
     std::vector<uint16_t> offs(sb ? size_t(t.n_dtiles) * G_pad * t.Dt
                                   : size_t(t.n_dtiles) * t.C_pad * t.Dt, 0);
-    std::vector<int4> bdesc(sb ? size_t(t.n_dtiles) * G_pad * kSbPatterns * 2 : 0,
-                            make_int4(0, 0, 0, 0));
+    // sub-band build blocks, per (DM tile, chunk); laid out with a common
+    // capacity once every chunk is known
+    const int n_chunks = (p->C + cch - 1) / cch;
+    std::vector<std::vector<int4>> blocks(sb ? size_t(t.n_dtiles) * n_chunks : 0);
     int64_t stage_max = 0, p_max = 0;
     for (int k = 0; k < t.n_dtiles; ++k) {
         const int d0 = k * t.Dt, d1 = std::min(p->D, d0 + t.Dt);
@@ -187,10 +190,14 @@ dd_status build_fwd_tables(dd_plan_s *p, const dd_variant &v, FwdTables *out) {
                 p_max = std::max(p_max, ch.p_elems);
                 const int g0 = c0 / kSbGroup;
                 const int ng = int(ch.poffs.size()) / t.Dt;
-                // build entries of the chunk, compacted: the valid (group, pattern)
-                // entries first, in partial-buffer order, each tagged with its
-                // group; the rest keep length 0
-                size_t at = (size_t(k) * G_pad + g0) * kSbPatterns * 2;
+                // Build blocks: every partial series is cut into blocks of up
+                // to 4 x 32 elements, {dst, r0, (r1-r0) | (r2-r0) << 16, (r3-r0)
+                // | group << 16 | channels << 20 | sub-blocks << 24} with the
+                // relative offsets as int16 (lane l of sub-block s builds
+                // dst[32 s + l] = sum_j w_j raw[r_j + 32 s + l]); the series'
+                // buffer lengths are whole 32-element sub-blocks, so no lane
+                // writes past its series.
+                std::vector<int4> &bl = blocks[size_t(k) * n_chunks + c0 / cch];
                 for (int g = 0; g < ng; ++g) {
                     for (int i = 0; i < t.Dt; ++i)
                         offs[(size_t(k) * G_pad + g0 + g) * t.Dt + i] =
@@ -198,28 +205,53 @@ dd_status build_fwd_tables(dd_plan_s *p, const dd_variant &v, FwdTables *out) {
                     for (int q = 0; q < kSbPatterns; ++q) {
                         const int *bd = &ch.bdesc[(size_t(g) * kSbPatterns + q) * 8];
                         if (bd[1] == 0) continue;
-                        bdesc[at] = make_int4(bd[0], bd[1], bd[2], bd[3]);
-                        bdesc[at + 1] = make_int4(bd[4], bd[5], bd[6], g);
-                        at += 2;
+                        const int gn = bd[6];
+                        int rel[4] = {0, 0, 0, 0};
+                        for (int j = 1; j < gn; ++j) {
+                            rel[j] = bd[2 + j] - bd[2];
+                            if (rel[j] < -32768 || rel[j] > 32767)
+                                return fail(DD_ERR_ARG, "channel windows too far apart for variant");
+                        }
+                        for (int u = 0; u < bd[1]; u += 128) {
+                            const int nsub = std::min(4, (bd[1] - u + 31) / 32);
+                            bl.push_back(make_int4(
+                                bd[0] + u, bd[2] + u,
+                                int((uint32_t(rel[1]) & 0xffffu) | (uint32_t(rel[2]) << 16)),
+                                int((uint32_t(rel[3]) & 0xffffu) | (uint32_t(g) << 16) |
+                                    (uint32_t(gn) << 20) | (uint32_t(nsub) << 24))));
+                        }
                     }
                 }
             }
         }
     }
+    std::vector<int4> bdesc;
+    if (sb) {
+        // Worker w of `parts` builds blocks w, w + parts, ... of a chunk in
+        // this order (series by series). (Assigning blocks longest first to
+        // the least-loaded worker measured slower on GB300.)
+        size_t cap = 1;
+        for (const auto &bl : blocks) cap = std::max(cap, bl.size());
+        t.n_blocks = int(cap);
+        bdesc.assign(blocks.size() * cap, make_int4(0, 0, 0, 0));  // 0 sub-blocks: no block
+        for (size_t i = 0; i < blocks.size(); ++i)
+            std::copy(blocks[i].begin(), blocks[i].end(), bdesc.begin() + i * cap);
+    }
     t.stage_elems = static_cast<int>(stage_max);
-    // 64 spare elements: register-window loads of a warp never leave the slot
+    // 64 spare elements: register-window loads of a warp and the last lanes of
+    // a build block never leave the slot
     t.stage_data_bytes = static_cast<int>(round_up((stage_max + 64) * elt, 16));
     // per slot after the window data: the chunk's tables, then its weights
     if (sb) {
         const int gpc = cch / kSbGroup;
         t.stage_offs_bytes = static_cast<int>(round_up(int64_t(gpc) * t.Dt * 2, 16)) +
-                             gpc * kSbPatterns * 32 + cch * 4;
+                             t.n_blocks * 16 + cch * 4;
         t.p_elems = static_cast<int>(round_up(p_max + 64, 4));
     } else {
         t.stage_offs_bytes = static_cast<int>(round_up(int64_t(cch) * t.Dt * 2, 16)) + cch * 4;
     }
     size_t p_bytes = 0;
-    if (v.kind == 2)  // 2 partial-sum slots, each with the chunk's trial offsets
+    if (v.kind == 2 || v.kind == 4)  // 2 partial-sum slots, each with the chunk's trial offsets
         p_bytes = size_t(2) * (size_t(t.p_elems) * 4 + size_t(cch / kSbGroup) * t.Dt * 2);
     if (v.kind == 3)  // 3 partial-sum slots, each with the chunk's trial offsets
         p_bytes = size_t(3) * (size_t(t.p_elems) * 4 + size_t(cch / kSbGroup) * t.Dt * 2);
@@ -260,13 +292,15 @@ namespace {
 
 // Candidate default variants, best first; the first that fits the plan is
 // used until dd_tune or dd_plan_set_variant picks another.
-// (Measured on GB300: the sub-band kind with 64-trial by 128-sample tiles and
-// 16 channels per stage leads on the Apertif-like and 512-channel setups; the
-// lane-strided kind 0 takes setups whose delay patterns are too varied for
-// sub-bands, e.g. wide low-frequency bands.)
+// (Measured on GB300: the wide sub-band kind with 64-trial by 256-sample
+// tiles and 16 channels per stage leads on the Apertif-like and 512-channel
+// setups, then kind 2's 64 x 128 tiles; the lane-strided kind 0 takes setups
+// whose delay patterns are too varied for sub-bands, e.g. wide
+// low-frequency bands.)
 const dd_variant kDefaults[] = {
-    {2, 8, 4, 8, 1, 16, 2}, {2, 8, 4, 4, 2, 8, 2}, {0, 4, 8, 4, 1, 8, 3}, {0, 4, 4, 4, 2, 8, 3},
-    {0, 4, 4, 4, 2, 4, 2},  {0, 2, 4, 4, 2, 4, 2},  {0, 4, 2, 4, 1, 4, 2},
+    {4, 4, 8, 16, 1, 16, 2}, {2, 8, 4, 8, 1, 16, 2}, {2, 8, 4, 4, 2, 8, 2},
+    {0, 4, 8, 4, 1, 8, 3},   {0, 4, 4, 4, 2, 8, 3},  {0, 4, 4, 4, 2, 4, 2},
+    {0, 2, 4, 4, 2, 4, 2},   {0, 4, 2, 4, 1, 4, 2},
 };
 
 }  // namespace
@@ -516,7 +550,9 @@ dd_status dd_variant_get(int32_t i, dd_variant *v) {
     const int ws = i % 6;
     i /= 6;
     const FwdKernelKey k = keys[size_t(i)];
-    *v = dd_variant{k.kind, k.dpt, k.spt, kShapes[ws][0], kShapes[ws][1], kCch[cc], kStages[st]};
+    // kind 4 runs twice the trial warps of each shape along DM
+    const int wdm = kShapes[ws][0] * (k.kind == 4 ? 2 : 1);
+    *v = dd_variant{k.kind, k.dpt, k.spt, wdm, kShapes[ws][1], kCch[cc], kStages[st]};
     return DD_OK;
 }
 

@@ -73,15 +73,25 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
 
 // Bounded wait for the phase with the given parity to complete. Returns false
 // (and sets kErrWaitTimeout in *err) if the budget ran out.
+//
+// `gave_up` (shared memory, nullable) is the CTA's give-up flag: a wait that
+// finds it set returns false at once, and a wait that runs out sets it. Once
+// one hand-off of a CTA is lost its barriers' phases are out of step (a later
+// parity test could pass on a stale phase), so every later wait of the CTA
+// fails fast and the caller skips the work that depended on it.
 __device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity, int *err,
-                                                  unsigned long long budget_ns = kWaitBudgetNs) {
+                                                  unsigned long long budget_ns = kWaitBudgetNs,
+                                                  volatile int *gave_up = nullptr) {
+    if (gave_up && *gave_up) return false;
     if (mbar_try_wait(bar, parity)) return true;
     const unsigned long long t0 = globaltimer_ns();
     for (;;) {
         for (int i = 0; i < 64; ++i)
             if (mbar_try_wait(bar, parity)) return true;
+        if (gave_up && *gave_up) return false;
         if (globaltimer_ns() - t0 > budget_ns) {
             if (err) atomicOr(err, kErrWaitTimeout);
+            if (gave_up) *gave_up = 1;
             return false;
         }
     }

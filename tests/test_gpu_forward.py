@@ -123,6 +123,55 @@ def test_every_variant_shape(dtype):
     plan.check_device()
 
 
+@pytest.mark.parametrize("dtype", DTYPES)
+def test_subband_kinds_every_shape(dtype):
+    """The sub-band kinds (2, 3, 4) need delay tables whose channel groups
+    share few relative patterns per DM tile, as Eq. 1 tables do; random
+    tables never fit them. Ragged everywhere: 102 channels (a last group of
+    2), 300 trials, 1100 samples, 2 beams."""
+    from paper_1601_05052_gb300 import compute_shifts
+    C, D, S = 102, 300, 1100
+    freqs = 1420.0 + np.arange(C) * (300.0 / 1024)
+    sh = compute_shifts(freqs, freqs[-1], 50e-6, np.arange(D) * 0.25).astype(np.int64)
+    rng = np.random.default_rng(78)
+    t_in = S + int(sh.max())
+    stride = synth.padded_stride(t_in, dtype)
+    xf = rng.standard_normal((2, C, stride)).astype(np.float32)
+    xf[:, :, t_in:] = np.nan
+    w = rng.uniform(-0.5, 1.5, C).astype(np.float32)
+    if dtype == "f32":
+        x = xf
+    elif dtype == "f16":
+        x = xf.astype(np.float16)
+    elif dtype == "bf16":
+        x = synth.to_bf16_bits(xf)
+    else:
+        x = synth.quantize_u8(np.nan_to_num(xf, nan=7.0))
+        w = synth.quantize_weights_q8(w)
+    plan = Plan(shifts=sh, n_out=S, batch=2, dtype=dtype)
+    xd, wd = to_dev(x, dtype), weights_dev(w, dtype)
+    if dtype == "u8":
+        ref = oracle.forward_u8(x, w, sh, S)
+    else:
+        ref, ab = oracle.forward(x, w, sh, S, dtype=dtype, with_absum=True)
+    ran = {}
+    for v in variants():
+        if v["kind"] not in (2, 3, 4) or v["stages"] == 4:
+            continue
+        try:
+            plan.variant = v
+        except Exception:
+            continue  # too many patterns for this tile shape
+        out = plan.execute(xd, wd).cpu().numpy()
+        if dtype == "u8":
+            np.testing.assert_array_equal(out.astype(np.int64), ref, err_msg=str(v))
+        else:
+            assert_float_parity(out, ref, ab, what=str(v))
+        ran[v["kind"]] = ran.get(v["kind"], 0) + 1
+    assert all(ran.get(k, 0) >= 3 for k in (2, 3, 4)), ran
+    plan.check_device()
+
+
 def test_execute_host_matches_device_path():
     rng = np.random.default_rng(9)
     sh, x, w = random_case(rng, 2, 30, 40, 800, 100, "f32")
