@@ -148,9 +148,15 @@ dd_status dd_execute(dd_plan plan, const void *d_in, const void *d_w, void *d_ou
                      void *stream);
 
 /* The same with HOST buffers: copies h_in and h_w to plan-owned device
- * buffers (allocated on first use), runs dd_execute on `stream`, copies the
- * result into h_out and synchronises the stream before returning. Pinned
- * host memory gives full copy bandwidth. */
+ * buffers (allocated on first use), runs the forward, delivers the result in
+ * h_out and synchronises `stream` before returning. With pinned (page-locked)
+ * buffers the output is written by the kernel straight into h_out over the
+ * CPU-GPU link, and the input is pulled in up to 8 segments of whole time
+ * tiles: segment s's forward launch starts as soon as the columns it needs
+ * (its samples plus the max delay) are on the device, while later columns are
+ * still in flight (plan-owned copy and compute streams, joined to `stream`).
+ * Pageable buffers are staged through plan-owned device mirrors. Not safe to
+ * call concurrently on one plan. */
 dd_status dd_execute_host(dd_plan plan, const void *h_in, const void *h_w, void *h_out,
                           void *stream);
 

@@ -191,6 +191,7 @@ dd_status configure(dd_batch_s *bt, const dd_variant &v) {
         a.offs = t.d_offs;
         a.bdesc = t.d_bdesc;
         a.n_blocks = t.n_blocks;
+        a.ttile0 = 0;
         a.p_elems = t.p_elems;
         a.err = p->d_err;
         bt->ba.item_start[i] = acc;

@@ -5,6 +5,7 @@
 // beam); the tile body is in dd_fwd_tile.cuh. Grid x runs over DM tiles so
 // that CTAs resident at the same time share time ranges and the input
 // windows they stage stay in L2.
+#include <algorithm>
 #include <atomic>
 
 #include "dd_fwd_tile.cuh"
@@ -19,8 +20,8 @@ __global__ void __launch_bounds__(fwd_max_threads(KIND), fwd_min_blocks(KIND, DP
     uint64_t *bars = reinterpret_cast<uint64_t *>(smem);
     fwd_init_barriers<KIND>(bars, a.stages);
     uint32_t kbase = 0;
-    fwd_tile_any<KIND, T, DPT, SPT>(a, blockIdx.x, blockIdx.y, blockIdx.z, bars, smem + 128,
-                                    kbase);
+    fwd_tile_any<KIND, T, DPT, SPT>(a, blockIdx.x, a.ttile0 + int(blockIdx.y), blockIdx.z, bars,
+                                    smem + 128, kbase);
 }
 
 // One CTA waits on an mbarrier that nothing arrives at, bounded by budget_ns.
@@ -41,6 +42,18 @@ __global__ void dd_copy16_kernel(uint4 *__restrict__ dst, const uint4 *__restric
     for (size_t i = blockIdx.x * size_t(blockDim.x) + threadIdx.x; i < n;
          i += size_t(gridDim.x) * blockDim.x)
         dst[i] = src[i];
+}
+
+// Copies columns [w0, w1) (16-byte words) of `rows` rows of `pitch` words
+// with all SMs.
+__global__ void dd_copy_cols16_kernel(uint4 *__restrict__ dst, const uint4 *__restrict__ src,
+                                      size_t rows, size_t pitch, size_t w0, size_t w1) {
+    const size_t width = w1 - w0, n = rows * width;
+    for (size_t i = blockIdx.x * size_t(blockDim.x) + threadIdx.x; i < n;
+         i += size_t(gridDim.x) * blockDim.x) {
+        const size_t r = i / width, c = w0 + i % width;
+        dst[r * pitch + c] = src[r * pitch + c];
+    }
 }
 
 // Device-side address of a page-locked host buffer, or null for pageable or
@@ -110,7 +123,10 @@ bool fwd_variant_compiled(int kind, int dpt, int spt) {
 }
 
 dd_status launch_forward(dd_plan_s *p, const FwdTables &t, const void *in, const void *w,
-                         void *out, cudaStream_t st) {
+                         void *out, cudaStream_t st, int ttile0, int n_ttiles) {
+    if (n_ttiles < 0) n_ttiles = t.n_ttiles - ttile0;
+    if (ttile0 < 0 || n_ttiles <= 0 || ttile0 + n_ttiles > t.n_ttiles)
+        return fail(DD_ERR_ARG, "time-tile range");
     FwdLaunchFn fn = pick_fn(p->dtype, t.v.kind, t.v.dm_per_thread, t.v.samples_per_thread);
     if (!fn) return fail(DD_ERR_UNSUPPORTED, "forward variant not compiled");
     FwdArgs a;
@@ -138,10 +154,81 @@ dd_status launch_forward(dd_plan_s *p, const FwdTables &t, const void *in, const
     a.n_blocks = t.n_blocks;
     a.p_elems = t.p_elems;
     a.err = p->d_err;
-    dim3 grid(unsigned(t.n_dtiles), unsigned(t.n_ttiles), unsigned(p->B));
+    a.ttile0 = ttile0;
+    dim3 grid(unsigned(t.n_dtiles), unsigned(n_ttiles), unsigned(p->B));
     dim3 block(unsigned(32 * (t.v.warps_dm * t.v.warps_time + extra_warps(t.v.kind))));
     cudaError_t e = fn(a, grid, block, t.smem_bytes, st);
     if (e != cudaSuccess) return cuda_fail(e, "forward launch");
+    return DD_OK;
+}
+
+// dd_execute_host with a pinned input: the input is pulled in segments of
+// whole time tiles, and segment s's forward launch starts as soon as its
+// columns are on the device. Segment s needs columns [0, min(T_in, end of its
+// last time tile + max shift)) of every row; each segment copies only the
+// columns beyond the previous one's, so the input crosses the link once. The
+// first increment (at least max shift columns) is pulled by an SM copy kernel
+// at the link's rate while nothing else runs; later increments go by the copy
+// engine, leaving the SMs to the forward launches, which alternate between
+// two streams so one segment's last wave overlaps the next segment's first.
+dd_status host_pipeline(dd_plan_s *p, const void *in_dev, const void *h_in, const void *h_w,
+                        void *out, cudaStream_t st) {
+    cudaError_t e = cudaSuccess;
+    for (int i = 0; i < 3 && e == cudaSuccess; ++i)
+        if (!p->hx_stream[i]) e = cudaStreamCreateWithFlags(&p->hx_stream[i], cudaStreamNonBlocking);
+    for (int i = 0; i < kHostSegments + 3 && e == cudaSuccess; ++i)
+        if (!p->hx_event[i]) e = cudaEventCreateWithFlags(&p->hx_event[i], cudaEventDisableTiming);
+    if (e != cudaSuccess) return cuda_fail(e, "pipeline streams");
+    cudaStream_t cs = p->hx_stream[0];
+    cudaEvent_t *ev = p->hx_event;
+    cudaEvent_t ev_start = ev[kHostSegments], ev_c1 = ev[kHostSegments + 1],
+                ev_c2 = ev[kHostSegments + 2];
+    const FwdTables &t = p->fwd;
+    const size_t elt = size_t(elt_bytes(p->dtype));
+    const size_t pitch_w = size_t(p->stride) * elt / 16;  // row pitch in 16-byte words
+    const size_t rows = size_t(p->B) * p->C;
+    const int nseg = std::min(kHostSegments, t.n_ttiles);
+    const int per = (t.n_ttiles + nseg - 1) / nseg;
+    // all streams start after the work already queued on the caller's stream
+    e = cudaEventRecord(ev_start, st);
+    for (int i = 0; i < 3 && e == cudaSuccess; ++i) e = cudaStreamWaitEvent(p->hx_stream[i], ev_start, 0);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(p->h_w_dev, h_w, size_t(p->C) * 4, cudaMemcpyHostToDevice, cs);
+    if (e != cudaSuccess) return cuda_fail(e, "pipeline start");
+    size_t w_done = 0;
+    for (int sgi = 0, tt = 0; tt < t.n_ttiles; ++sgi, tt += per) {
+        const int n_t = std::min(per, t.n_ttiles - tt);
+        const long long t_end = std::min<long long>(p->S, (long long)(tt + n_t) * t.Ts);
+        const long long cols = std::min<long long>(p->T_in, t_end + p->max_shift);
+        const size_t w_need = std::min(pitch_w, (size_t(cols) * elt + 15) / 16);
+        if (w_need > w_done) {
+            if (sgi == 0) {
+                dd_copy_cols16_kernel<<<4 * p->sm_count, 256, 0, cs>>>(
+                    static_cast<uint4 *>(p->h_in_dev), static_cast<const uint4 *>(in_dev), rows,
+                    pitch_w, w_done, w_need);
+                e = cudaGetLastError();
+            } else {
+                const size_t off = w_done * 16;
+                e = cudaMemcpy2DAsync(static_cast<unsigned char *>(p->h_in_dev) + off, pitch_w * 16,
+                                      static_cast<const unsigned char *>(h_in) + off, pitch_w * 16,
+                                      (w_need - w_done) * 16, rows, cudaMemcpyHostToDevice, cs);
+            }
+            if (e != cudaSuccess) return cuda_fail(e, "input segment copy");
+            w_done = w_need;
+        }
+        cudaStream_t ks = p->hx_stream[1 + (sgi & 1)];
+        e = cudaEventRecord(ev[sgi], cs);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(ks, ev[sgi], 0);
+        if (e != cudaSuccess) return cuda_fail(e, "pipeline event");
+        dd_status s = launch_forward(p, t, p->h_in_dev, p->h_w_dev, out, ks, tt, n_t);
+        if (s != DD_OK) return s;
+    }
+    // the caller's stream waits for both compute streams
+    e = cudaEventRecord(ev_c1, p->hx_stream[1]);
+    if (e == cudaSuccess) e = cudaEventRecord(ev_c2, p->hx_stream[2]);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(st, ev_c1, 0);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(st, ev_c2, 0);
+    if (e != cudaSuccess) return cuda_fail(e, "pipeline join");
     return DD_OK;
 }
 
@@ -189,20 +276,18 @@ dd_status dd_execute_host(dd_plan p, const void *h_in, const void *h_w, void *h_
         if (e != cudaSuccess) return cuda_fail(e, "cudaMalloc(host mirrors)");
     }
     cudaError_t e = cudaSuccess;
+    void *out = out_dev ? out_dev : p->h_out_dev;
     if (in_dev && aligned16(in_dev)) {
-        const int grid = 4 * p->sm_count;
-        dd_copy16_kernel<<<grid, 256, 0, st>>>(static_cast<uint4 *>(p->h_in_dev),
-                                               static_cast<const uint4 *>(in_dev), in_bytes / 16);
-        e = cudaGetLastError();
+        dd_status s = host_pipeline(p, in_dev, h_in, h_w, out, st);
+        if (s != DD_OK) return s;
     } else {
         e = cudaMemcpyAsync(p->h_in_dev, h_in, in_bytes, cudaMemcpyHostToDevice, st);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(p->h_w_dev, h_w, w_bytes, cudaMemcpyHostToDevice, st);
+        if (e != cudaSuccess) return cuda_fail(e, "input upload");
+        dd_status s = launch_forward(p, p->fwd, p->h_in_dev, p->h_w_dev, out, st);
+        if (s != DD_OK) return s;
     }
-    if (e == cudaSuccess)
-        e = cudaMemcpyAsync(p->h_w_dev, h_w, w_bytes, cudaMemcpyHostToDevice, st);
-    if (e != cudaSuccess) return cuda_fail(e, "input upload");
-    void *out = out_dev ? out_dev : p->h_out_dev;
-    dd_status s = launch_forward(p, p->fwd, p->h_in_dev, p->h_w_dev, out, st);
-    if (s != DD_OK) return s;
     if (!out_dev) e = cudaMemcpyAsync(h_out, p->h_out_dev, out_bytes, cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     if (e != cudaSuccess) return cuda_fail(e, "output download / sync");

@@ -103,6 +103,7 @@ struct FwdArgs {
     int Dt, Ts, C_pad, cch, stages, warps_dm;
     int stage_data_bytes, stage_offs_bytes;
     int n_dtiles, n_ttiles, B;
+    int ttile0;  // one-shot launches: time tile of grid row 0 (a launch may cover a range)
     const int4 *desc;
     const uint16_t *offs;
     const int4 *bdesc;  // sub-band kinds: build blocks [n_dtiles][n_chunks][n_blocks]

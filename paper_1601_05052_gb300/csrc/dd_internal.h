@@ -35,6 +35,9 @@ inline int align_elems(dd_dtype t) { return 16 / elt_bytes(t); }
 //                 0}
 //   offs[k][c][i] = smem element offset of sample t0 of trial k*Dt + i
 //                   in channel c (= smem_off + shift - win_start)
+// Input segments of dd_execute_host's copy/compute pipeline.
+constexpr int kHostSegments = 8;
+
 struct FwdTables {
     dd_variant v{};
     int Dt = 0, Ts = 0;
@@ -95,6 +98,10 @@ struct dd_plan_s {
 
     // device mirrors for dd_execute_host, allocated on first use
     void *h_in_dev = nullptr, *h_w_dev = nullptr, *h_out_dev = nullptr;
+    // dd_execute_host's input pipeline: a copy stream, two compute streams
+    // and one event per input segment (created on first use)
+    cudaStream_t hx_stream[3] = {nullptr, nullptr, nullptr};
+    cudaEvent_t hx_event[dd::kHostSegments + 3] = {};
 
     std::mutex mu;
 };
@@ -120,7 +127,8 @@ dd_status check_variant_shape(const dd_variant &v);
 
 // Enqueue the forward kernel with the plan's current tables.
 dd_status launch_forward(dd_plan_s *p, const FwdTables &t, const void *in, const void *w,
-                         void *out, cudaStream_t st);
+                         void *out, cudaStream_t st,
+                         int ttile0 = 0, int n_ttiles = -1);
 
 // Adjoint
 dd_status ensure_adj_state(dd_plan_s *p);

@@ -493,6 +493,10 @@ void dd_plan_destroy(dd_plan p) {
     free_adj_state(&p->adj);
     if (p->d_err) cudaFree(p->d_err);
     if (p->d_shifts) cudaFree(p->d_shifts);
+    for (cudaEvent_t &ev : p->hx_event)
+        if (ev) cudaEventDestroy(ev);
+    for (cudaStream_t &xs : p->hx_stream)
+        if (xs) cudaStreamDestroy(xs);
     if (p->h_in_dev) cudaFree(p->h_in_dev);
     if (p->h_w_dev) cudaFree(p->h_w_dev);
     if (p->h_out_dev) cudaFree(p->h_out_dev);

@@ -192,6 +192,35 @@ def test_execute_host_matches_device_path():
         assert torch.equal(dev, hout)
 
 
+@pytest.mark.parametrize("dtype", ["f32", "u8"])
+def test_execute_host_segmented_pipeline(dtype):
+    """Pinned input with many time tiles: the input is pulled in segments (an
+    SM copy for the first, the copy engine for the rest) and each segment's
+    forward starts once its columns are in; results equal the device path.
+    Also a sub-band variant (Eq. 1 table) and a repeated call."""
+    from paper_1601_05052_gb300 import compute_shifts
+    rng = np.random.default_rng(12)
+    sh, x, w = random_case(rng, 2, 36, 40, 9000, 700, dtype)
+    plan = Plan(shifts=sh, n_out=9000, batch=2, dtype=dtype)
+    freqs = 1420.0 + np.arange(64) * (300.0 / 1024)
+    sh2 = compute_shifts(freqs, freqs[-1], 50e-6, np.arange(128) * 0.25).astype(np.int64)
+    plan2 = Plan(shifts=sh2, n_out=7000, batch=1, dtype=dtype)
+    t_in2 = 7000 + int(sh2.max())
+    x2 = rng.integers(0, 255, (1, 64, synth.padded_stride(t_in2, dtype))).astype(
+        np.uint8 if dtype == "u8" else np.float32)
+    w2 = w[:1].repeat(64) if dtype == "u8" else rng.uniform(0.5, 1.5, 64).astype(np.float32)
+    for pl, xx, ww in ((plan, x, w), (plan2, x2, w2)):
+        dev = pl.execute(to_dev(xx, dtype), weights_dev(ww, dtype)).cpu()
+        hx = torch.from_numpy(np.ascontiguousarray(xx)).pin_memory()
+        hw = torch.from_numpy(np.ascontiguousarray(ww)).pin_memory()
+        hout = torch.empty(pl.out_shape, dtype=dev.dtype).pin_memory()
+        for _ in range(2):
+            hout.zero_()
+            pl.execute_host(hx, hw, hout)
+            assert torch.equal(dev, hout), pl.variant
+    assert plan2.variant["kind"] in (2, 4)
+
+
 def test_tuned_variant_stays_correct():
     rng = np.random.default_rng(10)
     sh, x, w = random_case(rng, 1, 96, 64, 3000, 400, "f32")
