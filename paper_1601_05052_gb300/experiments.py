@@ -26,6 +26,7 @@ variants that do not fit an instance are not meaningful for it. Inputs are
 seeded N(0,1) noise (performance does not depend on the values).
 
     python -m paper_1601_05052_gb300.experiments --setup apertif [--dm0]
+    python -m paper_1601_05052_gb300.experiments --setup all --markdown
 """
 import argparse
 import json
@@ -123,14 +124,49 @@ def run(name, dm0_only=False, instances=None, log=sys.stderr):
             "fixed": dict(zip(configs[0].keys(), fixed)) if fixed else None, "instances": rows}
 
 
+def markdown(results):
+    """One table row per instance from the results of run() for the four
+    experiments (Apertif and LOFAR, each with real DMs and with DM = 0)."""
+    by = {(r["setup"], r["dm0_only"]): {i["n_dm"]: i for i in r["instances"]} for r in results}
+    ap = by.get(("apertif", False), {})
+    cols = [("apertif", True), ("lofar", False), ("lofar", True)]
+    lines = ["| D | Apertif best GFLOP/s | mean | SNR | Chebyshev | tuned / fixed | "
+             "Apertif DM=0 best | LOFAR best | LOFAR DM=0 best |",
+             "|---|---|---|---|---|---|---|---|---|"]
+    ns = sorted(set().union(*[set(v) for v in by.values()])) if by else []
+    for n in ns:
+        a = ap.get(n)
+        cells = [str(n)]
+        if a:
+            cells += ["%.0f" % a["best_gflops"], "%.0f" % a["mean_gflops"], "%.2f" % a["snr"],
+                      "%.2f" % a["chebyshev"],
+                      "%.2f" % a["speedup_tuned_over_fixed"] if "speedup_tuned_over_fixed" in a
+                      else "-"]
+        else:
+            cells += ["-"] * 5
+        for key in cols:
+            i = by.get(key, {}).get(n)
+            cells.append("%.0f" % i["best_gflops"] if i else "-")
+        lines.append("| " + " | ".join(cells) + " |")
+    return "\n".join(lines)
+
+
 def main(argv=None):
     ap = argparse.ArgumentParser()
-    ap.add_argument("--setup", choices=sorted(SETUPS), default="apertif")
+    ap.add_argument("--setup", choices=sorted(SETUPS) + ["all"], default="apertif")
     ap.add_argument("--dm0", action="store_true", help="every trial DM = 0 (Section IV-C)")
     ap.add_argument("--max-log2-dm", type=int, default=12)
+    ap.add_argument("--markdown", action="store_true",
+                    help="print the results as one markdown table (with --setup all)")
     a = ap.parse_args(argv)
-    res = run(a.setup, a.dm0, [2 ** k for k in range(1, a.max_log2_dm + 1)])
-    print(json.dumps(res))
+    instances = [2 ** k for k in range(1, a.max_log2_dm + 1)]
+    if a.setup == "all":
+        res = [run(name, dm0, instances) for name in ("apertif", "lofar") for dm0 in (False, True)]
+    else:
+        res = [run(a.setup, a.dm0, instances)]
+    print(json.dumps(res if len(res) > 1 else res[0]))
+    if a.markdown:
+        print(markdown(res))
 
 
 if __name__ == "__main__":
