@@ -59,6 +59,15 @@ def _args():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-extras", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--only", choices=["uneven_u8", "uneven_f16", "uneven_f32", "f32_96beams",
+                                       "differentiable"],
+                    help="run one secondary workload alone (for profiling its kernels)")
+    ap.add_argument("--no-tune", action="store_true",
+                    help="with --only: keep the plans' starting variants (the built-in default, "
+                         "or the DD_TUNE_CACHE entry an earlier tuned run recorded)")
+    ap.add_argument("--variant", default=None,
+                    help="with --only uneven_*/f32_96beams: JSON forward variant to use instead "
+                         "of tuning (e.g. one a tuned run printed)")
     ap.add_argument("--tune-ms", type=int, default=0,
                     help="auto-tune the forward variant for this budget first (0 = no)")
     return ap.parse_args()
@@ -239,69 +248,89 @@ def run_reference(args):
 
 # ---------------------------------------------------------------- our arm
 
-def _extras(torch, flush, peaks, steps):
-    """Secondary measurement points (rank 0, one GPU)."""
+def _rand_input(torch, g, p, seed, dtype):
+    g.manual_seed(seed)
+    xf = torch.randn(p.in_shape, generator=g, device="cuda", dtype=torch.float32)
+    if dtype == "u8":
+        return (128.0 + 16.0 * xf).round_().clamp_(0, 255).to(torch.uint8)
+    return xf.to({"f32": torch.float32, "f16": torch.float16, "bf16": torch.bfloat16}[dtype])
+
+
+def _case_uneven(torch, flush, n_rep, dtypes=("u8", "f16", "f32"), tune=True, variant=None):
+    """Uneven-beam batch: 96 x (64 ch) + 32 x (256 ch, low frequency); 8-bit
+    and FP16 as one graph-captured persistent launch, FP32 as plain launches."""
     import synth
-    from paper_1601_05052_gb300 import Batch, Plan, dedisperse
-    out = {}
+    from paper_1601_05052_gb300 import Batch, Plan
     g = torch.Generator(device="cuda")
-    n_rep = max(3, min(20, steps // 10))
-
-    def rand_input(p, seed, dtype):
-        g.manual_seed(seed)
-        xf = torch.randn(p.in_shape, generator=g, device="cuda", dtype=torch.float32)
-        if dtype == "u8":
-            return (128.0 + 16.0 * xf).round_().clamp_(0, 255).to(torch.uint8)
-        return xf.to({"f32": torch.float32, "f16": torch.float16, "bf16": torch.bfloat16}[dtype])
-
-    # uneven-beam batch: 96 x (64 ch) + 32 x (256 ch, low frequency)
     hi, lo = synth.setup("cfg4_hi"), synth.setup("cfg4_lo")
     units = hi.batch * hi.n_dm * hi.n_out + lo.batch * lo.n_dm * lo.n_out
-    res = {}
-    for dtype in ("u8", "f16", "f32"):
+    res, used = {}, {}
+    for dtype in dtypes:
         plans = [Plan.from_setup(s, dtype=dtype) for s in (hi, lo)]
-        xs = [rand_input(p, 40 + i, dtype) for i, p in enumerate(plans)]
+        xs = [_rand_input(torch, g, p, 40 + i, dtype) for i, p in enumerate(plans)]
         ws = [torch.ones(p.n_chan, dtype=p.w_dtype, device="cuda") for p in plans]
         outs = [torch.empty(p.out_shape, dtype=p.out_dtype, device="cuda") for p in plans]
         if dtype == "f32":  # the plain form: one dd_execute launch per setup
             fn = lambda: [p.execute(x, w, o) for p, x, w, o in zip(plans, xs, ws, outs)]
+            used[dtype] = [p.variant for p in plans]
         else:
             bt = Batch(plans)
-            bt.tune(budget_ms=15000)
+            if variant:
+                bt.variant = variant
+            elif tune:
+                bt.tune(budget_ms=15000)
             fn = lambda bt=bt: bt.execute(xs, ws, outs)
+            used[dtype] = bt.variant
         t = statistics.median(_time_steps(fn, n_rep, 2, flush, torch))
         res[dtype] = units / (t * 1e-3)
         del xs, outs
         torch.cuda.empty_cache()
-    out["uneven_beams"] = {
-        "workload": "96 beams x (64 ch, 64 DM, 4096 samples) + 32 beams x (256 ch 120-180 MHz, "
-                    "2000 DM, 10000 samples)",
-        "batched_u8_graph": res["u8"], "batched_f16_graph": res["f16"],
-        "plain_f32_launches": res["f32"],
-        "speedup_u8_vs_f32": res["u8"] / res["f32"], "speedup_f16_vs_f32": res["f16"] / res["f32"],
-        "unit": UNIT}
+    out = {"workload": "96 beams x (64 ch, 64 DM, 4096 samples) + 32 beams x (256 ch 120-180 "
+                       "MHz, 2000 DM, 10000 samples)", "unit": UNIT, "variants": used}
+    for dtype in dtypes:
+        out["plain_f32_launches" if dtype == "f32" else "batched_%s_graph" % dtype] = res[dtype]
+    if "f32" in res:
+        for dtype in dtypes:
+            if dtype != "f32":
+                out["speedup_%s_vs_f32" % dtype] = res[dtype] / res["f32"]
+    return out
 
-    # HBM-bound point: 96 beams of the 64-channel setup in FP32
+
+def _case_96beams(torch, flush, n_rep, peaks, tune=True, variant=None):
+    """The cfg1 shape at 96 beams in FP32, the point where HBM could bind."""
+    import synth
+    from paper_1601_05052_gb300 import Plan
+    g = torch.Generator(device="cuda")
     s = synth.setup("cfg1x96")
     p = Plan.from_setup(s)
-    p.tune(budget_ms=8000)
-    x = rand_input(p, 7, "f32")
+    if variant:
+        p.variant = variant
+    elif tune:
+        p.tune(budget_ms=8000)
+    x = _rand_input(torch, g, p, 7, "f32")
     w = torch.ones(p.n_chan, device="cuda")
     o = torch.empty(p.out_shape, device="cuda")
     t = statistics.median(_time_steps(lambda: p.execute(x, w, o), n_rep, 2, flush, torch))
     comp = (x.numel() * 4 + o.numel() * 4) / (t * 1e-3) / 1e9
-    out["f32_96beams_64ch"] = {"value": s.batch * s.n_dm * s.n_out / (t * 1e-3), "unit": UNIT,
-                               "ms": t, "variant": p.variant, "effective_hbm_gbs": comp,
-                               "hbm_frac": comp / peaks["hbm_gbs"]}
-    del x, o
+    return {"value": s.batch * s.n_dm * s.n_out / (t * 1e-3), "unit": UNIT, "ms": t,
+            "variant": p.variant, "effective_hbm_gbs": comp, "hbm_frac": comp / peaks["hbm_gbs"]}
 
-    # differentiable workload: forward + backward (grad_in and grad_w)
+
+def _case_differentiable(torch, flush, n_rep, tune=True):
+    """16 beams x 512 ch x 1024 DM x 8192: forward, adjoint alone (grad_in and
+    grad_w of a full cotangent) and forward + backward of a windowed loss."""
+    import synth
+    from paper_1601_05052_gb300 import Plan, dedisperse
+    g = torch.Generator(device="cuda")
     s = synth.setup("cfg5")
     p = Plan.from_setup(s)
-    p.tune(budget_ms=8000)
-    p.tune_adjoint(budget_ms=8000)
-    x = rand_input(p, 9, "f32").requires_grad_(True)
+    rep_adj = None
+    if tune:
+        p.tune(budget_ms=8000)
+        rep_adj = p.tune_adjoint(budget_ms=8000)
+    x = _rand_input(torch, g, p, 9, "f32").requires_grad_(True)
     w = torch.ones(p.n_chan, device="cuda", requires_grad=True)
+    gout = torch.randn(p.out_shape, generator=g, device="cuda")
 
     def fwd_bwd():
         y = dedisperse(p, x, w)
@@ -309,12 +338,42 @@ def _extras(torch, flush, peaks, steps):
 
     tf = statistics.median(_time_steps(lambda: p.execute(x.detach(), w.detach()), n_rep, 2, flush,
                                        torch))
+    ta = statistics.median(_time_steps(lambda: p.adjoint(gout, w.detach(), x.detach()), n_rep, 2,
+                                       flush, torch))
     tb = statistics.median(_time_steps(fwd_bwd, n_rep, 2, flush, torch))
     units = s.batch * s.n_dm * s.n_out
-    out["differentiable_16beams"] = {"forward": units / (tf * 1e-3),
-                                     "forward_backward": units / (tb * 1e-3), "unit": UNIT,
-                                     "forward_ms": tf, "forward_backward_ms": tb}
-    return out
+    return {"forward": units / (tf * 1e-3), "forward_backward": units / (tb * 1e-3), "unit": UNIT,
+            "forward_ms": tf, "adjoint_ms": ta, "forward_backward_ms": tb,
+            "variant": p.variant, "adjoint_variant": rep_adj["best"] if rep_adj else None}
+
+
+def _extras(torch, flush, peaks, steps):
+    """Secondary measurement points (rank 0, one GPU)."""
+    n_rep = max(3, min(20, steps // 10))
+    return {"uneven_beams": _case_uneven(torch, flush, n_rep),
+            "f32_96beams_64ch": _case_96beams(torch, flush, n_rep, peaks),
+            "differentiable_16beams": _case_differentiable(torch, flush, n_rep)}
+
+
+def run_only(args):
+    """One secondary workload by itself (its own timed loop, args.steps
+    repetitions): a short command line for profiling that row's kernels."""
+    import torch
+    torch.cuda.set_device(0)
+    peaks, _ = _peaks()
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+    n = max(1, args.steps)
+    tune = not args.no_tune
+    variant = json.loads(args.variant) if args.variant else None
+    if args.only.startswith("uneven_"):
+        out = _case_uneven(torch, flush, n, dtypes=(args.only.split("_", 1)[1],), tune=tune,
+                           variant=variant)
+    elif args.only == "f32_96beams":
+        out = _case_96beams(torch, flush, n, peaks, tune=tune, variant=variant)
+    else:
+        out = _case_differentiable(torch, flush, n, tune=tune)
+    print(json.dumps({"case": args.only, "steps": n, **out}), flush=True)
+    return 0
 
 
 def run_ours(args):
@@ -439,6 +498,8 @@ def main():
     args = _args()
     if args.impl == "reference":
         return run_reference(args)
+    if args.only:
+        return run_only(args)
     return run_ours(args)
 
 

@@ -71,9 +71,19 @@ typedef struct dd_stream_s *dd_stream;
  *         input from shared memory.
  * kind 1: a thread owns samples_per_thread (odd) consecutive samples and
  *         keeps, per channel, the union window of its warp's trials in
- *         registers, serving every trial of the warp from it. */
+ *         registers, serving every trial of the warp from it.
+ * kind 2: sub-band partial sums: per group of 4 adjacent channels the CTA
+ *         builds, once per chunk, the weighted 4-channel sum series of each
+ *         distinct relative delay pattern of its trials, and every trial adds
+ *         one series value per group (lane-strided); plus one producer warp.
+ * kind 3: kind 2 with 4 dedicated builder warps (warp-specialised).
+ * kind 4: kind 2 in CTAs of up to 16 trial warps (one CTA per SM).
+ * kind 5: kind 0 that reuses the loaded operands for a trial whose delay in
+ *         the channel equals the previous trial's.
+ * Results do not depend on the variant beyond FP32 summation order (8-bit
+ * input: bit-identical). */
 typedef struct {
-    int32_t kind;                /* 0 lane-strided, 1 register window      */
+    int32_t kind;                /* 0..5, see above                         */
     int32_t dm_per_thread;       /* DMs accumulated per thread (registers) */
     int32_t samples_per_thread;  /* samples accumulated per thread          */
     int32_t warps_dm;            /* warps along the DM axis of a CTA        */

@@ -36,6 +36,9 @@
 //  kind 3, warp-specialised sub-band: kind 2's arithmetic with 4 extra
 //    builder warps; mbarriers on the staging slots and on 3 partial-sum
 //    slots replace every CTA-wide barrier.
+//  kind 5, lane-strided with shared delays: kind 0, but a trial whose delay
+//    in the channel equals the previous trial's reuses the operands already
+//    in registers.
 #pragma once
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
@@ -51,7 +54,8 @@
 // DM tile can span 128 trials and amortise each partial series over more of them.
 #define DD_FWD_KEYS(X)                                                                    \
     X(0, 2, 4) X(0, 4, 2) X(0, 4, 4) X(0, 8, 2) X(0, 8, 4) X(0, 4, 8) X(1, 8, 9) X(2, 4, 4) \
-        X(2, 4, 8) X(2, 8, 4) X(2, 8, 2) X(3, 8, 4) X(3, 4, 8) X(3, 8, 2) X(4, 8, 4) X(4, 4, 8)
+        X(2, 4, 8) X(2, 8, 4) X(2, 8, 2) X(3, 8, 4) X(3, 4, 8) X(3, 8, 2) X(4, 8, 4) X(4, 4, 8) \
+            X(5, 4, 8) X(5, 8, 4)
 
 namespace dd {
 
@@ -145,18 +149,17 @@ __device__ __forceinline__ void compute_barrier(int n) {
 }
 
 // Packed FP32 pair arithmetic of sm_100-class GPUs (one instruction for two
-// lanes' worth of adds / fmas): a += b and d = a * b + c element-wise.
+// lanes' worth of adds / fmas, each rounded to nearest like the scalar
+// forms): a += b and d = a * b + d element-wise.
 __device__ __forceinline__ void add2(float &a0, float &a1, float b0, float b1) {
-    asm("{\n\t.reg .b64 x, y;\n\tmov.b64 x, {%0, %1};\n\tmov.b64 y, {%2, %3};\n\t"
-        "add.rn.f32x2 x, x, y;\n\tmov.b64 {%0, %1}, x;\n\t}"
-        : "+f"(a0), "+f"(a1)
-        : "f"(b0), "f"(b1));
+    const float2 r = __fadd2_rn(make_float2(a0, a1), make_float2(b0, b1));
+    a0 = r.x;
+    a1 = r.y;
 }
 __device__ __forceinline__ void fma2(float &d0, float &d1, float a0, float a1, float b0, float b1) {
-    asm("{\n\t.reg .b64 x, y, z;\n\tmov.b64 x, {%2, %3};\n\tmov.b64 y, {%4, %5};\n\t"
-        "mov.b64 z, {%0, %1};\n\tfma.rn.f32x2 z, x, y, z;\n\tmov.b64 {%0, %1}, z;\n\t}"
-        : "+f"(d0), "+f"(d1)
-        : "f"(a0), "f"(a1), "f"(b0), "f"(b1));
+    const float2 r = __ffma2_rn(make_float2(a0, a1), make_float2(b0, b1), make_float2(d0, d1));
+    d0 = r.x;
+    d1 = r.y;
 }
 
 // ------------------------------------------------------------------ staging
@@ -265,8 +268,13 @@ __device__ __forceinline__ void store_lane_strided(const FwdArgs &a, const Acc (
 
 // ------------------------------------------------------------------ kinds 0 and 1
 
-// kind 0: lane-strided samples, one shared-memory read per add.
-template <typename T, int DPT, int SPT>
+// kind 0: lane-strided samples, one shared-memory read per add. kind 5
+// (REUSE): the same, but a trial whose delay in the channel equals the
+// previous trial's adds the operands already loaded for it; adjacent trials
+// often share a channel's delay at low DMs and high frequencies, so this
+// saves shared-memory reads there (it is a separate kernel because the test
+// and branch slow down setups where no trials share a delay).
+template <typename T, int DPT, int SPT, bool REUSE = false>
 struct LaneStrided {
     using Acc = typename Elem<T>::Acc;
     using Wt = typename Elem<T>::W;
@@ -275,11 +283,25 @@ struct LaneStrided {
     __device__ static void channel(Acc (&acc)[DPT][SPT], const T *sdata, int lane_base,
                                    const int (&o)[DPT], Wt wc) {
         const T *s = sdata + lane_base;
+        if constexpr (REUSE) {
+            Acc v[SPT];
 #pragma unroll
-        for (int i = 0; i < DPT; ++i) {
-            const T *src = s + o[i];
+            for (int i = 0; i < DPT; ++i) {
+                if (i == 0 || o[i] != o[i - 1]) {
+                    const T *src = s + o[i];
 #pragma unroll
-            for (int j = 0; j < SPT; ++j) acc[i][j] += wc * Elem<T>::val(src[32 * j]);
+                    for (int j = 0; j < SPT; ++j) v[j] = Elem<T>::val(src[32 * j]);
+                }
+#pragma unroll
+                for (int j = 0; j < SPT; ++j) acc[i][j] += wc * v[j];
+            }
+        } else {
+#pragma unroll
+            for (int i = 0; i < DPT; ++i) {
+                const T *src = s + o[i];
+#pragma unroll
+                for (int j = 0; j < SPT; ++j) acc[i][j] += wc * Elem<T>::val(src[32 * j]);
+            }
         }
     }
 };
@@ -376,8 +398,8 @@ template <int KIND, typename T, int DPT, int SPT>
 __device__ __forceinline__ void fwd_tile(const FwdArgs &a, int dtile, int ttile, int b,
                                          uint64_t *bars, unsigned char *stage0,
                                          uint32_t &kbase) {
-    using P = typename std::conditional<KIND == 1, RegWindow<T, DPT, SPT>,
-                                        LaneStrided<T, DPT, SPT>>::type;
+    using P = typename std::conditional<
+        KIND == 1, RegWindow<T, DPT, SPT>, LaneStrided<T, DPT, SPT, KIND == 5>>::type;
     using Acc = typename Elem<T>::Acc;
     using Wt = typename Elem<T>::W;
     uint64_t *full = bars;
@@ -459,7 +481,8 @@ __device__ __forceinline__ void fwd_tile(const FwdArgs &a, int dtile, int ttile,
 // raw[r_j + 32 s + l]. Worker `part` of `parts` takes blocks part, part +
 // parts, ...; the next block's descriptor is loaded while the current one is
 // built, and all of a block's operand loads are issued before its
-// arithmetic. Blocks with 0 sub-blocks are capacity padding.
+// arithmetic. Blocks with 0 sub-blocks are capacity padding; they sit after
+// every real block of the chunk, so a worker stops at its first one.
 template <typename T>
 __device__ __forceinline__ void sb_build_blocks(typename Elem<T>::Acc *P, const T *raw,
                                                 const int4 *blk, const typename Elem<T>::W *sw,
@@ -473,7 +496,8 @@ __device__ __forceinline__ void sb_build_blocks(typename Elem<T>::Acc *P, const 
         const int bn = b + parts;
         const int4 dn = bn < n_blocks ? blk[bn] : make_int4(0, 0, 0, 0);
         const int nsub = (d.w >> 24) & 7;
-        if (nsub) {
+        if (!nsub) break;
+        {
             const int g = (d.w >> 16) & 3, gn = (d.w >> 20) & 7;
             const int4 wv = *reinterpret_cast<const int4 *>(sw + 4 * g);
             const Wt w[4] = {__builtin_bit_cast(Wt, wv.x), __builtin_bit_cast(Wt, wv.y),
@@ -559,13 +583,20 @@ __device__ __forceinline__ void sb_trials(Acc (&acc)[DPT][SPT], const Acc *Pl,
                 o[2 * i] = int(ow[g].w[i] & 0xffffu);
                 o[2 * i + 1] = int(ow[g].w[i] >> 16);
             }
+            // trials of a thread that share the group's series and offset
+            // (same pattern, same base delay) reuse the loaded values
+            Acc v[SPT];
 #pragma unroll
             for (int i = 0; i < DPT; ++i) {
                 const Acc *src = Pl + o[i];
                 if constexpr (std::is_same<Acc, float>::value && SPT % 2 == 0) {
+                    if (i == 0 || o[i] != o[i - 1]) {
+#pragma unroll
+                        for (int j = 0; j < SPT; ++j) v[j] = src[32 * j];
+                    }
 #pragma unroll
                     for (int j = 0; j < SPT; j += 2)
-                        add2(acc[i][j], acc[i][j + 1], src[32 * j], src[32 * (j + 1)]);
+                        add2(acc[i][j], acc[i][j + 1], v[j], v[j + 1]);
                 } else {
 #pragma unroll
                     for (int j = 0; j < SPT; ++j) acc[i][j] += src[32 * j];

@@ -4,7 +4,8 @@
 // kind 0: lane-strided accumulation from the staged channel windows;
 // kind 1: register windows; kind 2: sub-band partial series (groups of four
 // channels) with a producer warp; kind 3: kind 2 with warp-specialised
-// builders; kind 4: kind 2 in CTAs of up to 16 trial warps.
+// builders; kind 4: kind 2 in CTAs of up to 16 trial warps; kind 5: kind 0
+// with operand reuse between trials that share a channel's delay.
 #pragma once
 
 #include <cuda_runtime.h>

@@ -172,6 +172,41 @@ def test_subband_kinds_every_shape(dtype):
     plan.check_device()
 
 
+@pytest.mark.parametrize("dtype", ["f32", "f16", "bf16"])
+def test_lane_strided_shared_delays(dtype):
+    """Kind 5 loads a channel's operands once for adjacent trials that share
+    its delay. An Eq. 1 table at low DMs (64 channels over 1400-1500 MHz,
+    DM step 0.5, 64 us) has many such pairs, mixed with channels that have
+    none; every CTA shape of kinds 0 and 5 must match the oracle."""
+    from paper_1601_05052_gb300 import compute_shifts
+    C, D, S = 64, 40, 777
+    freqs = 1400.0 + np.arange(C) * (100.0 / C)
+    sh = compute_shifts(freqs, freqs[-1], 64e-6, np.arange(D) * 0.5).astype(np.int64)
+    assert (sh[1:] == sh[:-1]).mean() > 0.2 and (sh[1:] != sh[:-1]).any()
+    rng = np.random.default_rng(79)
+    t_in = S + int(sh.max())
+    stride = synth.padded_stride(t_in, dtype)
+    xf = rng.standard_normal((2, C, stride)).astype(np.float32)
+    xf[:, :, t_in:] = np.nan
+    w = rng.uniform(-0.5, 1.5, C).astype(np.float32)
+    x = {"f32": xf, "f16": xf.astype(np.float16), "bf16": synth.to_bf16_bits(xf)}[dtype]
+    plan = Plan(shifts=sh, n_out=S, batch=2, dtype=dtype)
+    xd, wd = to_dev(x, dtype), weights_dev(w, dtype)
+    ref, ab = oracle.forward(x, w, sh, S, dtype=dtype, with_absum=True)
+    n = {0: 0, 5: 0}
+    for v in variants():
+        if v["kind"] not in n or v["stages"] == 4:
+            continue
+        try:
+            plan.variant = v
+        except Exception:
+            continue
+        assert_float_parity(plan.execute(xd, wd).cpu().numpy(), ref, ab, what=str(v))
+        n[v["kind"]] += 1
+    assert n[0] >= 20 and n[5] >= 6, n
+    plan.check_device()
+
+
 def test_execute_host_matches_device_path():
     rng = np.random.default_rng(9)
     sh, x, w = random_case(rng, 2, 30, 40, 800, 100, "f32")
