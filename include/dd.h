@@ -221,6 +221,15 @@ dd_status dd_tune(dd_plan plan, int32_t budget_ms, dd_tune_report *rep);
  * dd_adjoint). Builds the adjoint's buffers if they do not exist yet. */
 dd_status dd_tune_adjoint(dd_plan plan, int32_t budget_ms, dd_tune_report *rep);
 
+/* The kernel variant the adjoint's transposed gather runs: read it, or pin
+ * one (e.g. a variant an earlier dd_tune_adjoint reported). FP32 plans only
+ * (DD_ERR_UNSUPPORTED otherwise); both build the adjoint's buffers if they
+ * do not exist yet. dd_adjoint_set_variant returns DD_ERR_ARG, leaving the
+ * current variant in place, if v does not fit the transposed plan; it
+ * synchronises the device (no launch may still read the old tables). */
+dd_status dd_adjoint_get_variant(dd_plan plan, dd_variant *v);
+dd_status dd_adjoint_set_variant(dd_plan plan, const dd_variant *v);
+
 /* ---- Batched uneven setups (many beams of several observation setups) ----
  * A batch groups n plans (different C, D, S, input types). dd_batch_execute
  * runs every plan's forward in ONE persistent kernel launch whose CTAs pull

@@ -151,6 +151,18 @@ class Plan:
         _lib.check(_lib_().dd_tune_adjoint(self._h, int(budget_ms), ctypes.byref(r)))
         return r.as_dict()
 
+    @property
+    def adjoint_variant(self):
+        """The kernel variant of the adjoint's transposed gather (FP32 plans)."""
+        v = Variant()
+        _lib.check(_lib_().dd_adjoint_get_variant(self._h, ctypes.byref(v)))
+        return v.as_dict()
+
+    @adjoint_variant.setter
+    def adjoint_variant(self, d):
+        v = Variant(**d) if isinstance(d, dict) else Variant(*d)
+        _lib.check(_lib_().dd_adjoint_set_variant(self._h, ctypes.byref(v)))
+
     def check_device(self):
         _lib.check(_lib_().dd_plan_check_device(self._h))
 

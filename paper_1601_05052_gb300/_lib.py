@@ -71,6 +71,8 @@ SIGNATURES = [
     ("dd_grad_w_noalloc", i32, [P, P, P, P, P]),
     ("dd_tune", i32, [P, i32, ctypes.POINTER(TuneReport)]),
     ("dd_tune_adjoint", i32, [P, i32, ctypes.POINTER(TuneReport)]),
+    ("dd_adjoint_get_variant", i32, [P, ctypes.POINTER(Variant)]),
+    ("dd_adjoint_set_variant", i32, [P, ctypes.POINTER(Variant)]),
     ("dd_debug_wait_timeout", i32, [P, i32, P]),
     ("dd_batch_create", i32, [ctypes.POINTER(P), i32, PP]),
     ("dd_batch_execute", i32, [P, PP, PP, PP, P]),

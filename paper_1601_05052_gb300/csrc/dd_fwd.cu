@@ -153,6 +153,7 @@ dd_status launch_forward(dd_plan_s *p, const FwdTables &t, const void *in, const
     a.bdesc = t.d_bdesc;
     a.n_blocks = t.n_blocks;
     a.p_elems = t.p_elems;
+    a.live = t.d_live;
     a.err = p->d_err;
     a.ttile0 = ttile0;
     dim3 grid(unsigned(t.n_dtiles), unsigned(n_ttiles), unsigned(p->B));

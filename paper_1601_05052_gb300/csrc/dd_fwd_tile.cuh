@@ -113,8 +113,19 @@ struct FwdArgs {
     const int4 *bdesc;  // sub-band kinds: build blocks [n_dtiles][n_chunks][n_blocks]
     int n_blocks;       // sub-band kinds
     int p_elems;        // sub-band kinds
+    // Optional [n_dtiles][n_ttiles] {first, end} range of the chunks whose
+    // staged windows reach the input's nonzero columns (plans that declare
+    // zero input borders, i.e. the adjoint's transposed gather); chunks
+    // outside it only add zeros and are skipped. Null: every chunk.
+    const int2 *live;
     int *err;
 };
+
+// The chunks a tile stages and sums: all of them, or the live range.
+__device__ __forceinline__ int2 chunk_range(const FwdArgs &a, int dtile, int ttile) {
+    if (!a.live) return make_int2(0, (a.C + a.cch - 1) / a.cch);
+    return a.live[(size_t)dtile * a.n_ttiles + ttile];
+}
 
 // Loads the DPT uint16 smem offsets of this warp's trials with one vector
 // load (4/8/16-byte aligned by construction of the tables).
@@ -179,10 +190,11 @@ struct Stager {
     unsigned char *stage0;
     int stage_bytes;
     bool subband;
+    int kc0;  // chunk k of the tile's loop is chunk kc0 + k of the plan
 
     // Descriptor of this lane's channel in chunk k (zero beyond the chunk).
     __device__ __forceinline__ int4 desc(int k, int lane) const {
-        const int c = k * a.cch + lane;
+        const int c = (kc0 + k) * a.cch + lane;
         return (lane < a.cch && c < a.C) ? desc_k[c] : make_int4(0, 0, 0, 0);
     }
 
@@ -192,7 +204,7 @@ struct Stager {
     __device__ __forceinline__ void issue(int k, int slot, int4 dsc, uint64_t *full,
                                           int lane) const {
         unsigned char *sb = stage0 + slot * stage_bytes;
-        const int c0 = k * a.cch;
+        const int c0 = (kc0 + k) * a.cch;
         const int nch = min(a.cch, a.C - c0);
         const long long g0 = t0 + dsc.x;
         uint32_t bytes = 0;
@@ -217,8 +229,8 @@ struct Stager {
                 const int g0i = c0 / kSbG;
                 bulk_g2s(tb, static_cast<const uint16_t *>(tab_k) + (size_t)g0i * a.Dt,
                          tab1_bytes, full);
-                bulk_g2s(tb + tab1_bytes, bdesc_k + (size_t)k * a.n_blocks, tab_bytes - tab1_bytes,
-                         full);
+                bulk_g2s(tb + tab1_bytes, bdesc_k + (size_t)(kc0 + k) * a.n_blocks,
+                         tab_bytes - tab1_bytes, full);
             }
             // the chunk's weights; a 16-byte granule never crosses a page, so
             // rounding the last chunk up stays inside the weight buffer's page
@@ -229,7 +241,7 @@ struct Stager {
 
 template <typename T>
 __device__ __forceinline__ Stager<T> make_stager(const FwdArgs &a, int dtile, int b, long long t0,
-                                                 unsigned char *stage0, bool subband) {
+                                                 unsigned char *stage0, bool subband, int kc0) {
     const int gpc = a.cch / kSbG;
     const int g_pad = a.C_pad / kSbG;
     Stager<T> s{a,
@@ -245,7 +257,8 @@ __device__ __forceinline__ Stager<T> make_stager(const FwdArgs &a, int dtile, in
                 subband ? uint32_t(gpc) * a.Dt * 2 : uint32_t(a.cch) * a.Dt * 2,
                 stage0,
                 a.stage_data_bytes + a.stage_offs_bytes,
-                subband};
+                subband,
+                kc0};
     return s;
 }
 
@@ -408,8 +421,9 @@ __device__ __forceinline__ void fwd_tile(const FwdArgs &a, int dtile, int ttile,
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int wd = warp % a.warps_dm, wt = warp / a.warps_dm;
     const long long t0 = (long long)ttile * a.Ts;
-    const int n_chunks = (a.C + a.cch - 1) / a.cch;
-    const Stager<T> st = make_stager<T>(a, dtile, b, t0, stage0, false);
+    const int2 kr = chunk_range(a, dtile, ttile);
+    const int n_chunks = kr.y - kr.x;
+    const Stager<T> st = make_stager<T>(a, dtile, b, t0, stage0, false, kr.x);
 
     // warp 0 stages chunk k, after the slot's previous chunk was released
     auto issue = [&](int k, int4 dsc) {
@@ -442,7 +456,7 @@ __device__ __forceinline__ void fwd_tile(const FwdArgs &a, int dtile, int ttile,
         const uint16_t *soffs =
             reinterpret_cast<const uint16_t *>(sb + a.stage_data_bytes) + wd * DPT;
         const Wt *sw = reinterpret_cast<const Wt *>(sb + a.stage_data_bytes + st.tab_bytes);
-        const int nch = min(a.cch, a.C - k * a.cch);
+        const int nch = min(a.cch, a.C - (kr.x + k) * a.cch);
         for (int cc = 0; cc < nch; ++cc) {
             int o[DPT];
             load_offsets<DPT>(soffs + cc * a.Dt, o);
@@ -628,8 +642,9 @@ __device__ __forceinline__ void fwd_tile_sb(const FwdArgs &a, int dtile, int tti
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int nc = int(blockDim.x >> 5) - 1;  // compute warps; warp nc produces
     const long long t0 = (long long)ttile * a.Ts;
-    const int n_chunks = (a.C + a.cch - 1) / a.cch;
-    const Stager<T> st = make_stager<T>(a, dtile, b, t0, stage0, true);
+    const int2 kr = chunk_range(a, dtile, ttile);
+    const int n_chunks = kr.y - kr.x;
+    const Stager<T> st = make_stager<T>(a, dtile, b, t0, stage0, true, kr.x);
     const uint32_t poffs_bytes = st.tab1_bytes;
     const int pslot_bytes = a.p_elems * int(sizeof(Acc)) + int(poffs_bytes);
     unsigned char *pslot0 = stage0 + S * st.stage_bytes;
@@ -692,7 +707,7 @@ __device__ __forceinline__ void fwd_tile_sb(const FwdArgs &a, int dtile, int tti
         unsigned char *pb = pslot0 + (kg & 1u) * pslot_bytes;
         Acc *P = reinterpret_cast<Acc *>(pb);
         uint16_t *poffs = reinterpret_cast<uint16_t *>(pb + a.p_elems * int(sizeof(Acc)));
-        const int ng = (min(a.cch, a.C - k * a.cch) + kSbG - 1) / kSbG;
+        const int ng = (min(a.cch, a.C - (kr.x + k) * a.cch) + kSbG - 1) / kSbG;
 
         if (ok) {
             sb_build_blocks<T>(P, raw, bd, sw, a.n_blocks, warp, nc, lane);
@@ -727,8 +742,9 @@ __device__ __forceinline__ void fwd_tile_ws(const FwdArgs &a, int dtile, int tti
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int nc = int(blockDim.x >> 5) - kWsBuilders;  // trial warps
     const long long t0 = (long long)ttile * a.Ts;
-    const int n_chunks = (a.C + a.cch - 1) / a.cch;
-    const Stager<T> st = make_stager<T>(a, dtile, b, t0, stage0, true);
+    const int2 kr = chunk_range(a, dtile, ttile);
+    const int n_chunks = kr.y - kr.x;
+    const Stager<T> st = make_stager<T>(a, dtile, b, t0, stage0, true, kr.x);
     const uint32_t poffs_bytes = st.tab1_bytes;
     const int pslot_bytes = a.p_elems * int(sizeof(Acc)) + int(poffs_bytes);
     unsigned char *pslot0 = stage0 + S * st.stage_bytes;
@@ -794,7 +810,7 @@ __device__ __forceinline__ void fwd_tile_ws(const FwdArgs &a, int dtile, int tti
         const unsigned char *pb = pslot0 + ps * pslot_bytes;
         const uint16_t *poffs =
             reinterpret_cast<const uint16_t *>(pb + a.p_elems * int(sizeof(Acc))) + wd * DPT;
-        const int ng = (min(a.cch, a.C - k * a.cch) + kSbG - 1) / kSbG;
+        const int ng = (min(a.cch, a.C - (kr.x + k) * a.cch) + kSbG - 1) / kSbG;
         sb_trials<Acc, DPT, SPT>(acc, reinterpret_cast<const Acc *>(pb) + lb, poffs, a.Dt, ng);
         __syncwarp();
         if (lane == 0) mbar_arrive(&empty_p[ps]);

@@ -57,6 +57,10 @@ struct FwdTables {
     int4 *d_bdesc = nullptr;
     int n_blocks = 0;
     int p_elems = 0;
+    // plans with a declared nonzero input column range only:
+    // [n_dtiles][n_ttiles] {first, end} chunks whose staged windows reach it
+    // (the hull of those chunks; the others add zeros and are skipped)
+    int2 *d_live = nullptr;
 };
 
 // Sub-band (kind 2) geometry: channels per group, distinct delay patterns a
@@ -86,6 +90,10 @@ struct dd_plan_s {
     dd_dtype dtype = DD_F32;
     int32_t max_shift = 0;
     std::vector<int32_t> shifts;  // [D][C]
+    // Input columns outside [nz_lo, nz_hi) of every row are known to be zero
+    // (set internally for the adjoint's transposed plan, whose input is the
+    // zero-bordered cotangent); nz_hi < 0: no such knowledge.
+    int64_t nz_lo = 0, nz_hi = -1;
 
     int device = 0;
     int sm_count = 0;

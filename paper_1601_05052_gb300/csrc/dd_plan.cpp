@@ -259,8 +259,44 @@ dd_status build_fwd_tables(dd_plan_s *p, const dd_variant &v, FwdTables *out) {
     if (t.smem_bytes > p->smem_optin)
         return fail(DD_ERR_ARG, "variant needs more shared memory than the device has");
 
+    // Live chunk ranges (plans whose input is zero outside [nz_lo, nz_hi) of
+    // each row): chunk j of DM tile k can add a nonzero term in time tile tt
+    // only if one of its channels' windows [t0 + ws, t0 + ws + len) meets the
+    // nonzero columns; per (k, tt) the hull of those chunks is kept.
+    std::vector<int2> live;
+    if (p->nz_hi >= 0) {
+        live.assign(size_t(t.n_dtiles) * t.n_ttiles, make_int2(0, 0));
+        for (int k = 0; k < t.n_dtiles; ++k)
+            for (int tt = 0; tt < t.n_ttiles; ++tt) {
+                const int64_t t0 = int64_t(tt) * t.Ts;
+                int first = -1, last = -1;
+                for (int j = 0; j < n_chunks; ++j) {
+                    bool any = false;
+                    for (int c = j * cch; c < std::min(p->C, (j + 1) * cch) && !any; ++c) {
+                        const int4 d = desc[size_t(k) * t.C_pad + c];
+                        any = t0 + d.x < p->nz_hi && t0 + d.x + d.y > p->nz_lo;
+                    }
+                    if (any) {
+                        if (first < 0) first = j;
+                        last = j;
+                    }
+                }
+                if (first >= 0) live[size_t(k) * t.n_ttiles + tt] = make_int2(first, last + 1);
+            }
+    }
+
     cudaError_t e = cudaMalloc(&t.d_desc, desc.size() * sizeof(int4));
     if (e != cudaSuccess) return cuda_fail(e, "cudaMalloc(desc)");
+    if (!live.empty()) {
+        e = cudaMalloc(&t.d_live, live.size() * sizeof(int2));
+        if (e == cudaSuccess)
+            e = cudaMemcpy(t.d_live, live.data(), live.size() * sizeof(int2),
+                           cudaMemcpyHostToDevice);
+        if (e != cudaSuccess) {
+            free_fwd_tables(&t);
+            return cuda_fail(e, "live chunk table");
+        }
+    }
     e = cudaMalloc(&t.d_offs, offs.size() * sizeof(uint16_t));
     if (e == cudaSuccess && sb) e = cudaMalloc(&t.d_bdesc, bdesc.size() * sizeof(int4));
     if (e == cudaSuccess)
@@ -283,9 +319,11 @@ void free_fwd_tables(FwdTables *t) {
     if (t->d_desc) cudaFree(t->d_desc);
     if (t->d_offs) cudaFree(t->d_offs);
     if (t->d_bdesc) cudaFree(t->d_bdesc);
+    if (t->d_live) cudaFree(t->d_live);
     t->d_desc = nullptr;
     t->d_offs = nullptr;
     t->d_bdesc = nullptr;
+    t->d_live = nullptr;
 }
 
 namespace {
