@@ -193,7 +193,7 @@ dd_status configure(dd_batch_s *bt, const dd_variant &v) {
         a.n_blocks = t.n_blocks;
         a.ttile0 = 0;
         a.p_elems = t.p_elems;
-        a.live = t.d_live;
+        a.live = nullptr;  // the persistent kernel sums every chunk
         a.err = p->d_err;
         bt->ba.item_start[i] = acc;
         acc += (long long)t.n_dtiles * t.n_ttiles * p->B;

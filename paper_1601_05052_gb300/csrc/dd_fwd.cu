@@ -13,15 +13,17 @@
 
 namespace dd {
 
-template <int KIND, typename T, int DPT, int SPT>
+// LIVE: the plan has a live-chunk table (the adjoint's transposed gather,
+// FP32 only); tiles sum only their live chunks.
+template <int KIND, typename T, int DPT, int SPT, bool LIVE>
 __global__ void __launch_bounds__(fwd_max_threads(KIND), fwd_min_blocks(KIND, DPT, SPT))
     dd_fwd_kernel(const FwdArgs a) {
     extern __shared__ __align__(128) unsigned char smem[];
     uint64_t *bars = reinterpret_cast<uint64_t *>(smem);
     fwd_init_barriers<KIND>(bars, a.stages);
     uint32_t kbase = 0;
-    fwd_tile_any<KIND, T, DPT, SPT>(a, blockIdx.x, a.ttile0 + int(blockIdx.y), blockIdx.z, bars,
-                                    smem + 128, kbase);
+    fwd_tile_any<KIND, T, DPT, SPT, LIVE>(a, blockIdx.x, a.ttile0 + int(blockIdx.y), blockIdx.z,
+                                          bars, smem + 128, kbase);
 }
 
 // One CTA waits on an mbarrier that nothing arrives at, bounded by budget_ns.
@@ -73,36 +75,38 @@ namespace {
 
 using FwdLaunchFn = cudaError_t (*)(const FwdArgs &, dim3, dim3, size_t, cudaStream_t);
 
-template <int KIND, typename T, int DPT, int SPT>
+template <int KIND, typename T, int DPT, int SPT, bool LIVE>
 cudaError_t launch_fwd_t(const FwdArgs &a, dim3 grid, dim3 block, size_t smem, cudaStream_t st) {
     // Raise the kernel's dynamic shared-memory limit once per size increase.
     static std::atomic<size_t> smem_set{0};
     if (smem > 48 * 1024 && smem > smem_set.load()) {
-        cudaError_t e = cudaFuncSetAttribute(dd_fwd_kernel<KIND, T, DPT, SPT>,
+        cudaError_t e = cudaFuncSetAttribute(dd_fwd_kernel<KIND, T, DPT, SPT, LIVE>,
                                              cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              int(smem));
         if (e != cudaSuccess) return e;
         smem_set.store(smem);
     }
-    dd_fwd_kernel<KIND, T, DPT, SPT><<<grid, block, smem, st>>>(a);
+    dd_fwd_kernel<KIND, T, DPT, SPT, LIVE><<<grid, block, smem, st>>>(a);
     return cudaGetLastError();
 }
 
-template <typename T>
+template <typename T, bool LIVE>
 FwdLaunchFn pick(int kind, int dpt, int spt) {
 #define DD_PICK(K_, D_, S_) \
-    if (kind == K_ && dpt == D_ && spt == S_) return &launch_fwd_t<K_, T, D_, S_>;
+    if (kind == K_ && dpt == D_ && spt == S_) return &launch_fwd_t<K_, T, D_, S_, LIVE>;
     DD_FWD_KEYS(DD_PICK)
 #undef DD_PICK
     return nullptr;
 }
 
-FwdLaunchFn pick_fn(dd_dtype t, int kind, int dpt, int spt) {
+// Live-chunk kernels exist for FP32 only (the adjoint's transposed gather).
+FwdLaunchFn pick_fn(dd_dtype t, int kind, int dpt, int spt, bool live) {
+    if (live) return t == DD_F32 ? pick<float, true>(kind, dpt, spt) : nullptr;
     switch (t) {
-        case DD_F32: return pick<float>(kind, dpt, spt);
-        case DD_F16: return pick<__half>(kind, dpt, spt);
-        case DD_BF16: return pick<__nv_bfloat16>(kind, dpt, spt);
-        case DD_U8: return pick<uint8_t>(kind, dpt, spt);
+        case DD_F32: return pick<float, false>(kind, dpt, spt);
+        case DD_F16: return pick<__half, false>(kind, dpt, spt);
+        case DD_BF16: return pick<__nv_bfloat16, false>(kind, dpt, spt);
+        case DD_U8: return pick<uint8_t, false>(kind, dpt, spt);
     }
     return nullptr;
 }
@@ -119,7 +123,7 @@ const std::vector<FwdKernelKey> &fwd_compiled_keys() {
 }
 
 bool fwd_variant_compiled(int kind, int dpt, int spt) {
-    return pick_fn(DD_F32, kind, dpt, spt) != nullptr;
+    return pick_fn(DD_F32, kind, dpt, spt, false) != nullptr;
 }
 
 dd_status launch_forward(dd_plan_s *p, const FwdTables &t, const void *in, const void *w,
@@ -127,7 +131,8 @@ dd_status launch_forward(dd_plan_s *p, const FwdTables &t, const void *in, const
     if (n_ttiles < 0) n_ttiles = t.n_ttiles - ttile0;
     if (ttile0 < 0 || n_ttiles <= 0 || ttile0 + n_ttiles > t.n_ttiles)
         return fail(DD_ERR_ARG, "time-tile range");
-    FwdLaunchFn fn = pick_fn(p->dtype, t.v.kind, t.v.dm_per_thread, t.v.samples_per_thread);
+    FwdLaunchFn fn = pick_fn(p->dtype, t.v.kind, t.v.dm_per_thread, t.v.samples_per_thread,
+                             t.d_live != nullptr);
     if (!fn) return fail(DD_ERR_UNSUPPORTED, "forward variant not compiled");
     FwdArgs a;
     a.in = in;

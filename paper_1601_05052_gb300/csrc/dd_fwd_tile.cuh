@@ -113,18 +113,20 @@ struct FwdArgs {
     const int4 *bdesc;  // sub-band kinds: build blocks [n_dtiles][n_chunks][n_blocks]
     int n_blocks;       // sub-band kinds
     int p_elems;        // sub-band kinds
-    // Optional [n_dtiles][n_ttiles] {first, end} range of the chunks whose
-    // staged windows reach the input's nonzero columns (plans that declare
-    // zero input borders, i.e. the adjoint's transposed gather); chunks
-    // outside it only add zeros and are skipped. Null: every chunk.
+    // [n_dtiles][n_ttiles] {first, end} range of the chunks whose staged
+    // windows reach the input's nonzero columns, for plans that declare zero
+    // input borders (the adjoint's transposed gather); chunks outside it only
+    // add zeros. Read only by kernels compiled with LIVE; null otherwise.
     const int2 *live;
     int *err;
 };
 
-// The chunks a tile stages and sums: all of them, or the live range.
+// The chunks a tile stages and sums: all of them, or (kernels compiled with
+// LIVE, launched for plans that have a live table) the live range.
+template <bool LIVE>
 __device__ __forceinline__ int2 chunk_range(const FwdArgs &a, int dtile, int ttile) {
-    if (!a.live) return make_int2(0, (a.C + a.cch - 1) / a.cch);
-    return a.live[(size_t)dtile * a.n_ttiles + ttile];
+    if constexpr (LIVE) return a.live[(size_t)dtile * a.n_ttiles + ttile];
+    return make_int2(0, (a.C + a.cch - 1) / a.cch);
 }
 
 // Loads the DPT uint16 smem offsets of this warp's trials with one vector
@@ -407,7 +409,7 @@ __device__ __forceinline__ void fwd_init_barriers(uint64_t *bars, int stages) {
 // through its slots; chunk kg uses slot kg % stages, and the n-th completion
 // of a slot's full/empty barrier belongs to chunk slot + n * stages, so the
 // phase parities carry over from tile to tile without re-initialisation.
-template <int KIND, typename T, int DPT, int SPT>
+template <int KIND, typename T, int DPT, int SPT, bool LIVE>
 __device__ __forceinline__ void fwd_tile(const FwdArgs &a, int dtile, int ttile, int b,
                                          uint64_t *bars, unsigned char *stage0,
                                          uint32_t &kbase) {
@@ -421,7 +423,7 @@ __device__ __forceinline__ void fwd_tile(const FwdArgs &a, int dtile, int ttile,
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int wd = warp % a.warps_dm, wt = warp / a.warps_dm;
     const long long t0 = (long long)ttile * a.Ts;
-    const int2 kr = chunk_range(a, dtile, ttile);
+    const int2 kr = chunk_range<LIVE>(a, dtile, ttile);
     const int n_chunks = kr.y - kr.x;
     const Stager<T> st = make_stager<T>(a, dtile, b, t0, stage0, false, kr.x);
 
@@ -630,7 +632,7 @@ __device__ __forceinline__ void sb_trials(Acc (&acc)[DPT][SPT], const Acc *Pl,
 // never overwrites what slower warps still read. (Replacing the barrier by
 // per-warp mbarrier hand-offs, so that a warp builds chunk k+1 before its
 // trials on chunk k, measured slower on GB300.)
-template <typename T, int DPT, int SPT>
+template <typename T, int DPT, int SPT, bool LIVE>
 __device__ __forceinline__ void fwd_tile_sb(const FwdArgs &a, int dtile, int ttile, int b,
                                             uint64_t *bars, unsigned char *stage0,
                                             uint32_t &kbase) {
@@ -642,7 +644,7 @@ __device__ __forceinline__ void fwd_tile_sb(const FwdArgs &a, int dtile, int tti
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int nc = int(blockDim.x >> 5) - 1;  // compute warps; warp nc produces
     const long long t0 = (long long)ttile * a.Ts;
-    const int2 kr = chunk_range(a, dtile, ttile);
+    const int2 kr = chunk_range<LIVE>(a, dtile, ttile);
     const int n_chunks = kr.y - kr.x;
     const Stager<T> st = make_stager<T>(a, dtile, b, t0, stage0, true, kr.x);
     const uint32_t poffs_bytes = st.tab1_bytes;
@@ -731,7 +733,7 @@ __device__ __forceinline__ void fwd_tile_sb(const FwdArgs &a, int dtile, int tti
 // bars[4..6] / bars[12..14]. A partial-sum slot holds the chunk's partial
 // series followed by its per-group trial offsets (copied out of the staging
 // slot so that slot can be refilled as soon as the builders are done).
-template <typename T, int DPT, int SPT>
+template <typename T, int DPT, int SPT, bool LIVE>
 __device__ __forceinline__ void fwd_tile_ws(const FwdArgs &a, int dtile, int ttile, int b,
                                             uint64_t *bars, unsigned char *stage0,
                                             uint32_t &kbase) {
@@ -742,7 +744,7 @@ __device__ __forceinline__ void fwd_tile_ws(const FwdArgs &a, int dtile, int tti
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int nc = int(blockDim.x >> 5) - kWsBuilders;  // trial warps
     const long long t0 = (long long)ttile * a.Ts;
-    const int2 kr = chunk_range(a, dtile, ttile);
+    const int2 kr = chunk_range<LIVE>(a, dtile, ttile);
     const int n_chunks = kr.y - kr.x;
     const Stager<T> st = make_stager<T>(a, dtile, b, t0, stage0, true, kr.x);
     const uint32_t poffs_bytes = st.tab1_bytes;
@@ -820,16 +822,16 @@ __device__ __forceinline__ void fwd_tile_ws(const FwdArgs &a, int dtile, int tti
 }
 
 // Dispatches a tile to the kind's body.
-template <int KIND, typename T, int DPT, int SPT>
+template <int KIND, typename T, int DPT, int SPT, bool LIVE = false>
 __device__ __forceinline__ void fwd_tile_any(const FwdArgs &a, int dtile, int ttile, int b,
                                              uint64_t *bars, unsigned char *stage0,
                                              uint32_t &kbase) {
     if constexpr (KIND == 2 || KIND == 4)
-        fwd_tile_sb<T, DPT, SPT>(a, dtile, ttile, b, bars, stage0, kbase);
+        fwd_tile_sb<T, DPT, SPT, LIVE>(a, dtile, ttile, b, bars, stage0, kbase);
     else if constexpr (KIND == 3)
-        fwd_tile_ws<T, DPT, SPT>(a, dtile, ttile, b, bars, stage0, kbase);
+        fwd_tile_ws<T, DPT, SPT, LIVE>(a, dtile, ttile, b, bars, stage0, kbase);
     else
-        fwd_tile<KIND, T, DPT, SPT>(a, dtile, ttile, b, bars, stage0, kbase);
+        fwd_tile<KIND, T, DPT, SPT, LIVE>(a, dtile, ttile, b, bars, stage0, kbase);
 }
 
 }  // namespace dd
