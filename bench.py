@@ -280,7 +280,7 @@ def _case_uneven(torch, flush, n_rep, dtypes=("u8", "f16", "f32"), tune=True, va
             elif tune:
                 bt.tune(budget_ms=15000)
             fn = lambda bt=bt: bt.execute(xs, ws, outs)
-            used[dtype] = bt.variant
+            used[dtype] = bt.plan_variants
         t = statistics.median(_time_steps(fn, n_rep, 2, flush, torch))
         res[dtype] = units / (t * 1e-3)
         del xs, outs

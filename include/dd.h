@@ -238,16 +238,30 @@ dd_status dd_adjoint_set_variant(dd_plan plan, const dd_variant *v);
  * pointers and stream (later calls with the same pointers replay it).
  * d_in[i], d_w[i], d_out[i] follow plan i's conventions. At most 16 plans;
  * they must share the input type and outlive the batch. Work items are taken
- * heaviest setup first; every plan runs with the batch's common variant. */
+ * heaviest setup first. One launch runs one compiled kernel: all plans share
+ * kind, dm_per_thread, samples_per_thread, stages and the number of trial
+ * warps (warps_dm * warps_time); each plan has its own split of those warps
+ * (its DM x time tile) and its own chans_per_stage. */
 dd_status dd_batch_create(dd_batch *out, int32_t n, const dd_plan *plans);
 dd_status dd_batch_execute(dd_batch batch, const void *const *d_in,
                            const void *const *d_w, void *const *d_out, void *stream);
-/* The batch's common variant; set rebuilds its tables and graph. */
+/* The batch's common variant; set gives every plan that variant and rebuilds
+ * the tables and graph (synchronises the device). */
 dd_status dd_batch_get_variant(dd_batch batch, dd_variant *v);
 dd_status dd_batch_set_variant(dd_batch batch, const dd_variant *v);
-/* Auto-tunes the common variant of a batch by timing the whole persistent
- * launch for every compiled variant that fits all of its plans (scratch
- * buffers allocated and freed here); same report as dd_tune. */
+/* The variant plan i (index into the plans given to dd_batch_create) runs in
+ * the batch. set changes only that plan's; DD_ERR_ARG, leaving every variant
+ * as it was, if v does not share kind, dm_per_thread, samples_per_thread,
+ * stages and warps_dm * warps_time with the other plans' or does not fit the
+ * plan. Synchronises the device. */
+dd_status dd_batch_get_plan_variant(dd_batch batch, int32_t i, dd_variant *v);
+dd_status dd_batch_set_plan_variant(dd_batch batch, int32_t i, const dd_variant *v);
+/* Auto-tunes a batch (Section IV-A's experiment applied to one launch):
+ * times the whole persistent launch for every compiled variant that fits all
+ * of its plans, keeps the fastest as the common variant, then tries each
+ * plan's other splits of the trial warps and chunk sizes in turn, keeping
+ * those that shorten the launch (scratch buffers allocated and freed here).
+ * The report (as dd_tune's) describes the common-variant sweep. */
 dd_status dd_batch_tune(dd_batch batch, int32_t budget_ms, dd_tune_report *rep);
 void dd_batch_destroy(dd_batch batch);
 

@@ -265,6 +265,20 @@ class Batch:
         v = Variant(**d) if isinstance(d, dict) else Variant(*d)
         _lib.check(_lib_().dd_batch_set_variant(self._h, ctypes.byref(v)))
 
+    def plan_variant(self, i):
+        """The variant plan i runs in this batch (its own tile split and chunk)."""
+        v = Variant()
+        _lib.check(_lib_().dd_batch_get_plan_variant(self._h, int(i), ctypes.byref(v)))
+        return v.as_dict()
+
+    def set_plan_variant(self, i, d):
+        v = Variant(**d) if isinstance(d, dict) else Variant(*d)
+        _lib.check(_lib_().dd_batch_set_plan_variant(self._h, int(i), ctypes.byref(v)))
+
+    @property
+    def plan_variants(self):
+        return [self.plan_variant(i) for i in range(len(self.plans))]
+
     def tune(self, budget_ms=0):
         r = TuneReport()
         _lib.check(_lib_().dd_batch_tune(self._h, int(budget_ms), ctypes.byref(r)))

@@ -78,6 +78,8 @@ SIGNATURES = [
     ("dd_batch_execute", i32, [P, PP, PP, PP, P]),
     ("dd_batch_get_variant", i32, [P, ctypes.POINTER(Variant)]),
     ("dd_batch_set_variant", i32, [P, ctypes.POINTER(Variant)]),
+    ("dd_batch_get_plan_variant", i32, [P, i32, ctypes.POINTER(Variant)]),
+    ("dd_batch_set_plan_variant", i32, [P, i32, ctypes.POINTER(Variant)]),
     ("dd_batch_tune", i32, [P, i32, ctypes.POINTER(TuneReport)]),
     ("dd_batch_destroy", None, [P]),
     ("dd_stream_create", i32, [ctypes.POINTER(P), P]),

@@ -7,12 +7,17 @@
 // all (plan, beam, DM tile, time tile) tiles, numbered plan by plan with the
 // DM tile fastest. A persistent grid (resident CTAs only) pulls items from a
 // device counter with atomicAdd, so uneven setups balance across SMs; plans
-// are ordered heaviest tile first so the tail is made of light tiles. Every
-// plan in a batch uses one common kernel variant (one block shape, register
-// tile and staging depth: a launch has a single register and shared-memory
-// budget), with its own staging tables for that variant. The counter reset
-// and the launch form a two-node CUDA graph, re-parameterised only when the
-// buffer pointers change.
+// are ordered heaviest tile first so the tail is made of light tiles. One
+// launch runs one compiled kernel (kind, DMs and samples per thread) with
+// one block size and staging depth, but each plan has its own tile shape
+// within it: its split of the trial warps along DM and time (so its DM x
+// time tile) and its channels per stage, with its own staging tables; the
+// batch tuner picks the common kernel first and then each plan's shape. A
+// CTA finishes a tile (every chunk consumed) before it takes the next item,
+// so tiles of plans with different slot layouts never overlap in shared
+// memory, and the common staging depth keeps the mbarrier phases of
+// consecutive tiles in step. The counter reset and the launch form a
+// two-node CUDA graph, re-parameterised only when the buffer pointers change.
 #include <algorithm>
 #include <chrono>
 #include <cmath>
@@ -106,7 +111,8 @@ struct dd_batch_s {
     std::vector<dd_plan> plans;   // in work-list order (heaviest tile first)
     std::vector<int> user_index;  // position of plans[i] in the caller's arrays
     dd_dtype dtype = DD_F32;
-    dd_variant v{};
+    dd_variant v{};                // the common variant the batch was set to
+    std::vector<dd_variant> pv;    // each plan's variant (work-list order)
     std::vector<dd::FwdTables> tabs;
     std::vector<dd::FwdArgs> h_args;
     dd::FwdArgs *d_args = nullptr;
@@ -131,15 +137,33 @@ void release_tables(dd_batch_s *bt) {
     bt->graph = nullptr;
 }
 
-// Builds tables, launch shape and graph for variant v (all plans must fit).
-dd_status configure(dd_batch_s *bt, const dd_variant &v) {
+// Per-plan variants can share one persistent launch when they agree on the
+// compiled kernel, the staging depth and the number of trial warps.
+bool launch_compatible(const dd_variant &a, const dd_variant &b) {
+    return a.kind == b.kind && a.dm_per_thread == b.dm_per_thread &&
+           a.samples_per_thread == b.samples_per_thread && a.stages == b.stages &&
+           a.warps_dm * a.warps_time == b.warps_dm * b.warps_time;
+}
+
+// Builds tables, launch shape and graph for the per-plan variants pv (work-
+// list order; every plan must fit its variant).
+dd_status configure(dd_batch_s *bt, const std::vector<dd_variant> &pv) {
+    if (pv.size() != bt->plans.size()) return fail(DD_ERR_ARG, "one variant per plan");
+    const dd_variant &v = pv.front();
+    for (const dd_variant &x : pv) {
+        if (!launch_compatible(v, x))
+            return fail(DD_ERR_ARG, "the plans of a batch must share kind, dm_per_thread, "
+                                    "samples_per_thread, stages and warps_dm * warps_time");
+        dd_status s = check_variant_shape(x);
+        if (s != DD_OK) return s;
+    }
     PersistentFn pf = pick_persistent(bt->dtype, v.kind, v.dm_per_thread, v.samples_per_thread);
     if (!pf.fn) return fail(DD_ERR_ARG, "variant not compiled");
     std::vector<FwdTables> tabs;
     size_t smem = 0;
-    for (dd_plan p : bt->plans) {
+    for (size_t i = 0; i < bt->plans.size(); ++i) {
         FwdTables t;
-        dd_status s = build_fwd_tables(p, v, &t);
+        dd_status s = build_fwd_tables(bt->plans[i], pv[i], &t);
         if (s != DD_OK) {
             for (auto &x : tabs) free_fwd_tables(&x);
             return s;
@@ -155,7 +179,7 @@ dd_status configure(dd_batch_s *bt, const dd_variant &v) {
     }
     release_tables(bt);
     bt->tabs = tabs;
-    bt->v = v;
+    bt->pv = pv;
     bt->smem = smem;
     bt->block = block;
     bt->grid = occ * bt->plans.front()->sm_count;
@@ -179,9 +203,9 @@ dd_status configure(dd_batch_s *bt, const dd_variant &v) {
         a.Dt = t.Dt;
         a.Ts = t.Ts;
         a.C_pad = t.C_pad;
-        a.cch = v.chans_per_stage;
-        a.stages = v.stages;
-        a.warps_dm = v.warps_dm;
+        a.cch = pv[size_t(i)].chans_per_stage;
+        a.stages = pv[size_t(i)].stages;
+        a.warps_dm = pv[size_t(i)].warps_dm;
         a.stage_data_bytes = t.stage_data_bytes;
         a.stage_offs_bytes = t.stage_offs_bytes;
         a.n_dtiles = t.n_dtiles;
@@ -227,6 +251,20 @@ dd_status configure(dd_batch_s *bt, const dd_variant &v) {
     if (e == cudaSuccess) e = cudaGraphInstantiate(&bt->exec, bt->graph, 0);
     if (e != cudaSuccess) return cuda_fail(e, "batch graph");
     return DD_OK;
+}
+
+// The same variant for every plan.
+dd_status configure(dd_batch_s *bt, const dd_variant &v) {
+    dd_status s = configure(bt, std::vector<dd_variant>(bt->plans.size(), v));
+    if (s == DD_OK) bt->v = v;
+    return s;
+}
+
+// Work-list position of the caller's plan index u, or -1.
+int worklist_pos(const dd_batch_s *bt, int u) {
+    for (size_t i = 0; i < bt->user_index.size(); ++i)
+        if (bt->user_index[i] == u) return int(i);
+    return -1;
 }
 
 double tile_cost(dd_plan p) {
@@ -335,6 +373,37 @@ dd_status dd_batch_set_variant(dd_batch bt, const dd_variant *v) {
     return configure(bt, *v);
 }
 
+dd_status dd_batch_get_plan_variant(dd_batch bt, int32_t i, dd_variant *v) {
+    if (!bt || !v) return fail(DD_ERR_ARG, "null argument");
+    const int j = worklist_pos(bt, i);
+    if (j < 0) return fail(DD_ERR_ARG, "plan index out of range");
+    *v = bt->pv[size_t(j)];
+    return DD_OK;
+}
+
+dd_status dd_batch_set_plan_variant(dd_batch bt, int32_t i, const dd_variant *v) {
+    if (!bt || !v) return fail(DD_ERR_ARG, "null argument");
+    const int j = worklist_pos(bt, i);
+    if (j < 0) return fail(DD_ERR_ARG, "plan index out of range");
+    std::vector<dd_variant> pv = bt->pv;
+    pv[size_t(j)] = *v;
+    for (const dd_variant &x : pv)
+        if (!launch_compatible(x, *v))
+            return fail(DD_ERR_ARG, "the plans of a batch must share kind, dm_per_thread, "
+                                    "samples_per_thread, stages and warps_dm * warps_time");
+    cudaError_t e = cudaDeviceSynchronize();
+    if (e != cudaSuccess) return cuda_fail(e, "cudaDeviceSynchronize");
+    const std::vector<dd_variant> old = bt->pv;
+    dd_status s = configure(bt, pv);
+    if (s != DD_OK) {
+        const dd_status keep = dd_get_last_error();
+        const std::string msg = dd_last_error_message();
+        configure(bt, old);  // the previous variants fitted; keep them
+        return fail(keep, msg);
+    }
+    return DD_OK;
+}
+
 dd_status dd_batch_tune(dd_batch bt, int32_t budget_ms, dd_tune_report *rep) {
     if (!bt) return fail(DD_ERR_ARG, "null batch");
     const size_t n = bt->plans.size();
@@ -380,8 +449,8 @@ dd_status dd_batch_tune(dd_batch bt, int32_t budget_ms, dd_tune_report *rep) {
         uw[size_t(u)] = ws[i];
         uout[size_t(u)] = outs[i];
     }
-    auto time_ms = [&](const dd_variant &v, double *ms) -> dd_status {
-        if (configure(bt, v) != DD_OK) return DD_OK;  // does not fit every plan
+    auto time_pv = [&](const std::vector<dd_variant> &pv, double *ms) -> dd_status {
+        if (configure(bt, pv) != DD_OK) return DD_OK;  // does not fit every plan
         bt->args_on_device = false;
         dd_status s = dd_batch_execute(bt, uin.data(), uw.data(), uout.data(), st);
         const int reps = 3;
@@ -398,11 +467,52 @@ dd_status dd_batch_tune(dd_batch bt, int32_t budget_ms, dd_tune_report *rep) {
         *ms = double(f) / reps;
         return DD_OK;
     };
+    auto time_ms = [&](const dd_variant &v, double *ms) -> dd_status {
+        return time_pv(std::vector<dd_variant>(n, v), ms);
+    };
+    const auto wall0 = std::chrono::steady_clock::now();
     const dd_variant start = bt->v;
     dd_variant best = start;
     dd_status s = sweep_variants(budget_ms, flop, time_ms, &best, rep);
+    // Per-setup tile shapes: with the common kernel and staging depth fixed,
+    // each plan in turn tries every split of the trial warps along DM and
+    // time and every chunk size, keeping what shortens the whole launch by
+    // more than 1 % (the paper's finding that no one configuration suits
+    // every setup, applied within one launch).
+    std::vector<dd_variant> pv(n, best);
+    if (s == DD_OK && n > 1) {
+        double cur = -1.0;
+        s = time_pv(pv, &cur);
+        const int tw = best.warps_dm * best.warps_time;
+        auto over = [&]() {
+            return budget_ms > 0 && std::chrono::duration<double, std::milli>(
+                                        std::chrono::steady_clock::now() - wall0)
+                                            .count() > 2.0 * budget_ms;
+        };
+        for (size_t j = 0; j < n && s == DD_OK && cur > 0 && !over(); ++j) {
+            for (int wdm = 1; wdm <= tw && s == DD_OK; ++wdm) {
+                if (tw % wdm) continue;
+                for (int cch : {4, 8, 16}) {
+                    std::vector<dd_variant> cand = pv;
+                    cand[j].warps_dm = wdm;
+                    cand[j].warps_time = tw / wdm;
+                    cand[j].chans_per_stage = cch;
+                    if (cand[j].warps_dm == pv[j].warps_dm && cand[j].chans_per_stage == cch)
+                        continue;
+                    double ms = -1.0;
+                    s = time_pv(cand, &ms);
+                    if (s != DD_OK) break;
+                    if (ms > 0 && ms < 0.99 * cur) {
+                        cur = ms;
+                        pv = cand;
+                    }
+                }
+            }
+        }
+    }
     cleanup();
-    dd_status s2 = configure(bt, s == DD_OK ? best : start);
+    dd_status s2 = s == DD_OK ? configure(bt, pv) : configure(bt, start);
+    if (s2 == DD_OK) bt->v = s == DD_OK ? best : start;
     if (s != DD_OK) return s;
     return s2;
 }

@@ -76,3 +76,78 @@ def test_batched_uneven_beams_u8_workload4_sampled():
             assert rep["n_tried"] >= 1
     for p in plans:
         p.check_device()
+
+
+@pytest.mark.parametrize("dtype", ["f32", "u8"])
+def test_per_plan_tile_shapes_in_one_launch(dtype):
+    """Each plan of a batch keeps its own split of the trial warps (its DM x
+    time tile) and its own chunk size inside the one persistent launch; the
+    results stay exact, and a variant that does not share the launch's
+    kernel, staging depth or warp count is refused without changing any."""
+    from paper_1601_05052_gb300 import DDError, compute_shifts
+    rng = np.random.default_rng(33)
+    cases, plans = [], []
+    # three uneven Eq. 1 tables (the sub-band kinds fit them)
+    for C, D, S, f0, bw in ((48, 64, 700, 1250.0, 300.0), (32, 40, 1500, 1400.0, 100.0),
+                            (20, 24, 900, 1300.0, 200.0)):
+        freqs = f0 + np.arange(C) * (bw / C)
+        sh = compute_shifts(freqs, freqs[-1], 100e-6, np.arange(D) * 0.25).astype(np.int64)
+        t_in = S + int(sh.max())
+        x = rng.standard_normal((2, C, synth.padded_stride(t_in, dtype))).astype(np.float32)
+        w = rng.uniform(0.5, 1.5, C).astype(np.float32)
+        if dtype == "u8":
+            x, w = synth.quantize_u8(x), synth.quantize_weights_q8(w)
+        cases.append((sh, x, w, S))
+    plans = [Plan(shifts=c[0], n_out=c[3], batch=c[1].shape[0], dtype=dtype) for c in cases]
+    batch = Batch(plans)
+    xs = [to_dev(c[1], dtype) for c in cases]
+    ws = [weights_dev(c[2], dtype) for c in cases]
+
+    def check(what):
+        outs = batch.execute(xs, ws)
+        for (sh, x, w, S), o in zip(cases, outs):
+            o = o.cpu().numpy()
+            if dtype == "u8":
+                np.testing.assert_array_equal(o.astype(np.int64), oracle.forward_u8(x, w, sh, S),
+                                              err_msg=what)
+            else:
+                ref, ab = oracle.forward(x, w, sh, S, dtype=dtype, with_absum=True)
+                assert_float_parity(o, ref, ab, what=what)
+
+    tried = 0
+    for kind, dpt, spt, tw in ((0, 4, 4, 8), (2, 4, 8, 8), (4, 4, 8, 16), (5, 4, 8, 8)):
+        base = dict(kind=kind, dm_per_thread=dpt, samples_per_thread=spt, warps_dm=2,
+                    warps_time=tw // 2, chans_per_stage=4, stages=2)
+        try:
+            batch.variant = base
+        except DDError:
+            continue  # a plan has too many delay patterns per DM tile for this sub-band shape
+        combos = [(wd, tw // wd, c) for wd in (1, 2, 4, 8, 16) if wd <= tw and tw % wd == 0
+                  for c in (4, 8, 16)]
+        for i in range(len(plans)):
+            # the first other shape (from a start that differs per plan) that fits plan i
+            for k in range(len(combos)):
+                wd, wt, c = combos[(5 * i + k) % len(combos)]
+                v = dict(base, warps_dm=wd, warps_time=wt, chans_per_stage=c)
+                if v == base:
+                    continue
+                try:
+                    batch.set_plan_variant(i, v)
+                except DDError:
+                    continue  # does not fit (e.g. a sub-band DM tile not a multiple of 8)
+                assert batch.plan_variant(i) == v
+                break
+        pv = batch.plan_variants
+        assert len({tuple(sorted(v.items())) for v in pv}) >= 2, pv  # shapes differ per plan
+        check("per-plan shapes, kind %d: %s" % (kind, pv))
+        tried += 1
+        before = batch.plan_variants
+        with pytest.raises(DDError):
+            batch.set_plan_variant(0, dict(base, stages=3))
+        with pytest.raises(DDError):
+            batch.set_plan_variant(1, dict(base, warps_dm=1, warps_time=1))
+        assert batch.plan_variants == before
+        check("after refused changes, kind %d" % kind)
+    assert tried == 4
+    for p in plans:
+        p.check_device()
