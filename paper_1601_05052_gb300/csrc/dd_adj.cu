@@ -8,8 +8,9 @@
 // (= sum_b sum_d sum_t g[b][d][t] * in[b][c][t + shift[d][c]]).
 //
 // The gather is itself a dedispersion with the roles of channels and trials
-// swapped: with M = the plan's largest delay and g' the cotangent rows padded
-// by M zeros in front (g'[b][d][u] = g[b][d][u - M], zero outside [M, M+S)),
+// swapped: with M = the plan's largest delay rounded up to a multiple of 4
+// and g' the cotangent rows padded by M zeros in front (g'[b][d][u] =
+// g[b][d][u - M], zero outside [M, M+S)),
 //     G[b][c][tau] = sum_d 1 * g'[b][d][tau + (M - shift[d][c])],
 // i.e. the forward with D "channels", C "trials", delays M - shift >= 0 and
 // unit weights, over tau < stride. So the adjoint runs the same tuned forward
@@ -17,8 +18,9 @@
 // knows that its input is zero outside columns [M, M + S): its tiles skip the
 // chunks of trials whose staged windows lie wholly in the zero borders
 // (about a fifth of the gather's work at 16 x 512 x 1024 x 8192). Per call:
-// one strided copy of g into the padded buffer (its zero borders are written
-// once), one forward launch writing G into gin (or scratch), and a fused
+// one copy kernel moving g into the padded buffer (its zero borders are
+// written once; M is a multiple of 4 so that rows move as 16-byte words when
+// S allows), one forward launch writing G into gin (or scratch), and a fused
 // epilogue that scales gin by w and forms each (beam, channel)'s share of
 // grad_w with a fixed-order block reduction; a last kernel adds the beams in
 // a fixed order, so results are bitwise reproducible.
@@ -85,6 +87,35 @@ __global__ void dd_gw_reduce_kernel(const float *part, int B, int C, float *gw) 
     gw[c] = float(s);
 }
 
+// g'[row][M + t] = g[row][t] for t < S: block item i copies columns
+// [i % nb * kPadCols, ...) of row i / nb; 16-byte words when both row
+// starts are 16-byte aligned, single floats otherwise.
+constexpr int kPadThreads = 256;
+constexpr int kPadCols = 4 * 4 * kPadThreads;  // floats per block item
+__global__ void __launch_bounds__(kPadThreads) dd_pad_rows_kernel(
+    float *__restrict__ gpad, const float *__restrict__ g, long long S, long long pitch,
+    long long M, long long nb, bool vec) {
+    const long long row = blockIdx.x / nb;
+    const long long c0 = (blockIdx.x % nb) * kPadCols;
+    const float *src = g + row * S;
+    float *dst = gpad + row * pitch + M;
+    if (vec) {
+        const float4 *s4 = reinterpret_cast<const float4 *>(src);
+        float4 *d4 = reinterpret_cast<float4 *>(dst);
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const long long c = c0 / 4 + threadIdx.x + k * kPadThreads;
+            if (c < S / 4) d4[c] = s4[c];
+        }
+    } else {
+#pragma unroll
+        for (int k = 0; k < 16; ++k) {
+            const long long c = c0 + threadIdx.x + k * kPadThreads;
+            if (c < S) dst[c] = src[c];
+        }
+    }
+}
+
 __global__ void dd_fill_kernel(float *p, long long n, float v) {
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
          i += (long long)gridDim.x * blockDim.x)
@@ -106,7 +137,7 @@ void free_adj_state(AdjState *a) {
 dd_status ensure_adj_state(dd_plan_s *p) {
     if (p->adj.plan) return DD_OK;
     AdjState a;
-    a.M = p->max_shift;
+    a.M = (p->max_shift + 3) / 4 * 4;
     std::vector<int32_t> sh(size_t(p->C) * p->D);
     for (int d = 0; d < p->D; ++d)
         for (int c = 0; c < p->C; ++c)
@@ -159,10 +190,13 @@ dd_status launch_adjoint(dd_plan_s *p, const float *g, const float *w, const flo
         G = a.gscr;
     }
     // g'[b][d][M + t] = g[b][d][t]; the zero borders were written at allocation
-    cudaError_t e = cudaMemcpy2DAsync(a.gpad + a.M, size_t(q->stride) * sizeof(float), g,
-                                      size_t(p->S) * sizeof(float), size_t(p->S) * sizeof(float),
-                                      size_t(p->B) * p->D, cudaMemcpyDeviceToDevice, st);
-    if (e != cudaSuccess) return cuda_fail(e, "cudaMemcpy2DAsync(padded cotangent)");
+    const long long rows = (long long)p->B * p->D;
+    const long long nb = (p->S + kPadCols - 1) / kPadCols;
+    const bool vec = p->S % 4 == 0 && a.M % 4 == 0 && q->stride % 4 == 0;
+    dd_pad_rows_kernel<<<unsigned(rows * nb), kPadThreads, 0, st>>>(a.gpad, g, p->S, q->stride,
+                                                                     a.M, nb, vec);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(e, "padded cotangent copy");
     dd_status s = launch_forward(q, q->fwd, a.gpad, a.ones, G, st);
     if (s != DD_OK) return s;
     dd_adj_epilogue<<<unsigned(size_t(p->B) * p->C), kEpiThreads, 0, st>>>(
