@@ -22,8 +22,8 @@ __global__ void __launch_bounds__(fwd_max_threads(KIND), fwd_min_blocks(KIND, DP
     uint64_t *bars = reinterpret_cast<uint64_t *>(smem);
     fwd_init_barriers<KIND>(bars, a.stages);
     uint32_t kbase = 0;
-    fwd_tile_any<KIND, T, DPT, SPT, LIVE>(a, blockIdx.x, a.ttile0 + int(blockIdx.y), blockIdx.z,
-                                          bars, smem + 128, kbase);
+    fwd_tile_any<KIND, T, DPT, SPT, LIVE>(a, a.dtile0 + int(blockIdx.x), a.ttile0 + int(blockIdx.y),
+                                          blockIdx.z, bars, smem + 128, kbase);
 }
 
 // One CTA waits on an mbarrier that nothing arrives at, bounded by budget_ns.
@@ -127,10 +127,14 @@ bool fwd_variant_compiled(int kind, int dpt, int spt) {
 }
 
 dd_status launch_forward(dd_plan_s *p, const FwdTables &t, const void *in, const void *w,
-                         void *out, cudaStream_t st, int ttile0, int n_ttiles) {
+                         void *out, cudaStream_t st, int ttile0, int n_ttiles, int dtile0,
+                         int n_dtiles) {
     if (n_ttiles < 0) n_ttiles = t.n_ttiles - ttile0;
     if (ttile0 < 0 || n_ttiles <= 0 || ttile0 + n_ttiles > t.n_ttiles)
         return fail(DD_ERR_ARG, "time-tile range");
+    if (n_dtiles < 0) n_dtiles = t.n_dtiles - dtile0;
+    if (dtile0 < 0 || n_dtiles <= 0 || dtile0 + n_dtiles > t.n_dtiles)
+        return fail(DD_ERR_ARG, "DM-tile range");
     FwdLaunchFn fn = pick_fn(p->dtype, t.v.kind, t.v.dm_per_thread, t.v.samples_per_thread,
                              t.d_live != nullptr);
     if (!fn) return fail(DD_ERR_UNSUPPORTED, "forward variant not compiled");
@@ -161,7 +165,8 @@ dd_status launch_forward(dd_plan_s *p, const FwdTables &t, const void *in, const
     a.live = t.d_live;
     a.err = p->d_err;
     a.ttile0 = ttile0;
-    dim3 grid(unsigned(t.n_dtiles), unsigned(n_ttiles), unsigned(p->B));
+    a.dtile0 = dtile0;
+    dim3 grid(unsigned(n_dtiles), unsigned(n_ttiles), unsigned(p->B));
     dim3 block(unsigned(32 * (t.v.warps_dm * t.v.warps_time + extra_warps(t.v.kind))));
     cudaError_t e = fn(a, grid, block, t.smem_bytes, st);
     if (e != cudaSuccess) return cuda_fail(e, "forward launch");
@@ -174,21 +179,23 @@ dd_status launch_forward(dd_plan_s *p, const FwdTables &t, const void *in, const
 // last time tile + max shift)) of every row; each segment copies only the
 // columns beyond the previous one's, so the input crosses the link once. The
 // first increment (at least max shift columns) is pulled by an SM copy kernel
-// at the link's rate while nothing else runs; later increments go by the copy
-// engine, leaving the SMs to the forward launches, which alternate between
-// two streams so one segment's last wave overlaps the next segment's first.
+// at the link's rate; its DM tiles whose delays stay within half the largest
+// (the low DMs) start on the columns they need while the rest of that
+// increment arrives. Later increments go by the copy engine, leaving the SMs
+// to the forward launches, which alternate between two streams so one
+// segment's last wave overlaps the next segment's first.
 dd_status host_pipeline(dd_plan_s *p, const void *in_dev, const void *h_in, const void *h_w,
                         void *out, cudaStream_t st) {
     cudaError_t e = cudaSuccess;
     for (int i = 0; i < 3 && e == cudaSuccess; ++i)
         if (!p->hx_stream[i]) e = cudaStreamCreateWithFlags(&p->hx_stream[i], cudaStreamNonBlocking);
-    for (int i = 0; i < kHostSegments + 3 && e == cudaSuccess; ++i)
+    for (int i = 0; i < kHostSegments + 4 && e == cudaSuccess; ++i)
         if (!p->hx_event[i]) e = cudaEventCreateWithFlags(&p->hx_event[i], cudaEventDisableTiming);
     if (e != cudaSuccess) return cuda_fail(e, "pipeline streams");
     cudaStream_t cs = p->hx_stream[0];
     cudaEvent_t *ev = p->hx_event;
     cudaEvent_t ev_start = ev[kHostSegments], ev_c1 = ev[kHostSegments + 1],
-                ev_c2 = ev[kHostSegments + 2];
+                ev_c2 = ev[kHostSegments + 2], ev_low = ev[kHostSegments + 3];
     const FwdTables &t = p->fwd;
     const size_t elt = size_t(elt_bytes(p->dtype));
     const size_t pitch_w = size_t(p->stride) * elt / 16;  // row pitch in 16-byte words
@@ -202,11 +209,50 @@ dd_status host_pipeline(dd_plan_s *p, const void *in_dev, const void *h_in, cons
         e = cudaMemcpyAsync(p->h_w_dev, h_w, size_t(p->C) * 4, cudaMemcpyHostToDevice, cs);
     if (e != cudaSuccess) return cuda_fail(e, "pipeline start");
     size_t w_done = 0;
+    auto words = [&](long long cols) {
+        return std::min(pitch_w, (size_t(std::min<long long>(p->T_in, cols)) * elt + 15) / 16);
+    };
     for (int sgi = 0, tt = 0; tt < t.n_ttiles; ++sgi, tt += per) {
         const int n_t = std::min(per, t.n_ttiles - tt);
         const long long t_end = std::min<long long>(p->S, (long long)(tt + n_t) * t.Ts);
         const long long cols = std::min<long long>(p->T_in, t_end + p->max_shift);
-        const size_t w_need = std::min(pitch_w, (size_t(cols) * elt + 15) / 16);
+        const size_t w_need = words(cols);
+        if (sgi == 0) {
+            // The first segment's leading DM tiles whose delays stay within half the largest
+            // need far fewer columns (delays grow with DM): pull those columns first and start
+            // their tiles while the rest of the segment's columns arrive.
+            int k1 = 0;
+            int32_t low_max = 0;
+            while (k1 < t.n_dtiles && 2 * int64_t(t.dtile_max_shift[size_t(k1)]) <= p->max_shift) {
+                low_max = std::max(low_max, t.dtile_max_shift[size_t(k1)]);
+                ++k1;
+            }
+            const size_t w_low = words(t_end + low_max);
+            if (k1 > 0 && k1 < t.n_dtiles && w_low < w_need) {
+                dd_copy_cols16_kernel<<<4 * p->sm_count, 256, 0, cs>>>(
+                    static_cast<uint4 *>(p->h_in_dev), static_cast<const uint4 *>(in_dev), rows,
+                    pitch_w, 0, w_low);
+                e = cudaGetLastError();
+                if (e == cudaSuccess) e = cudaEventRecord(ev_low, cs);
+                if (e == cudaSuccess) e = cudaStreamWaitEvent(p->hx_stream[2], ev_low, 0);
+                if (e != cudaSuccess) return cuda_fail(e, "first input columns");
+                dd_status s = launch_forward(p, t, p->h_in_dev, p->h_w_dev, out, p->hx_stream[2],
+                                             tt, n_t, 0, k1);
+                if (s != DD_OK) return s;
+                dd_copy_cols16_kernel<<<4 * p->sm_count, 256, 0, cs>>>(
+                    static_cast<uint4 *>(p->h_in_dev), static_cast<const uint4 *>(in_dev), rows,
+                    pitch_w, w_low, w_need);
+                e = cudaGetLastError();
+                if (e == cudaSuccess) e = cudaEventRecord(ev[0], cs);
+                if (e == cudaSuccess) e = cudaStreamWaitEvent(p->hx_stream[1], ev[0], 0);
+                if (e != cudaSuccess) return cuda_fail(e, "first input segment");
+                w_done = w_need;
+                s = launch_forward(p, t, p->h_in_dev, p->h_w_dev, out, p->hx_stream[1], tt, n_t,
+                                   k1, t.n_dtiles - k1);
+                if (s != DD_OK) return s;
+                continue;
+            }
+        }
         if (w_need > w_done) {
             if (sgi == 0) {
                 dd_copy_cols16_kernel<<<4 * p->sm_count, 256, 0, cs>>>(

@@ -108,6 +108,7 @@ struct FwdArgs {
     int stage_data_bytes, stage_offs_bytes;
     int n_dtiles, n_ttiles, B;
     int ttile0;  // one-shot launches: time tile of grid row 0 (a launch may cover a range)
+    int dtile0;  // one-shot launches: DM tile of grid column 0
     const int4 *desc;
     const uint16_t *offs;
     const int4 *bdesc;  // sub-band kinds: build blocks [n_dtiles][n_chunks][n_blocks]

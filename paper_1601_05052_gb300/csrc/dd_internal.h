@@ -57,6 +57,8 @@ struct FwdTables {
     int4 *d_bdesc = nullptr;
     int n_blocks = 0;
     int p_elems = 0;
+    // largest delay of each DM tile (over its trials and all channels)
+    std::vector<int32_t> dtile_max_shift;
     // plans with a declared nonzero input column range only:
     // [n_dtiles][n_ttiles] {first, end} chunks whose staged windows reach it
     // (the hull of those chunks; the others add zeros and are skipped)
@@ -109,7 +111,7 @@ struct dd_plan_s {
     // dd_execute_host's input pipeline: a copy stream, two compute streams
     // and one event per input segment (created on first use)
     cudaStream_t hx_stream[3] = {nullptr, nullptr, nullptr};
-    cudaEvent_t hx_event[dd::kHostSegments + 3] = {};
+    cudaEvent_t hx_event[dd::kHostSegments + 4] = {};
 
     std::mutex mu;
 };
@@ -133,10 +135,12 @@ dd_status build_fwd_tables(dd_plan_s *p, const dd_variant &v, FwdTables *out);
 void free_fwd_tables(FwdTables *t);
 dd_status check_variant_shape(const dd_variant &v);
 
-// Enqueue the forward kernel with the plan's current tables.
+// Enqueue the forward kernel with the plan's current tables, over time tiles
+// [ttile0, ttile0 + n_ttiles) and DM tiles [dtile0, dtile0 + n_dtiles)
+// (-1: to the end).
 dd_status launch_forward(dd_plan_s *p, const FwdTables &t, const void *in, const void *w,
-                         void *out, cudaStream_t st,
-                         int ttile0 = 0, int n_ttiles = -1);
+                         void *out, cudaStream_t st, int ttile0 = 0, int n_ttiles = -1,
+                         int dtile0 = 0, int n_dtiles = -1);
 
 // Adjoint
 dd_status ensure_adj_state(dd_plan_s *p);

@@ -152,6 +152,7 @@ dd_status build_fwd_tables(dd_plan_s *p, const dd_variant &v, FwdTables *out) {
     const int n_chunks = (p->C + cch - 1) / cch;
     std::vector<std::vector<int4>> blocks(sb ? size_t(t.n_dtiles) * n_chunks : 0);
     int64_t stage_max = 0, p_max = 0;
+    t.dtile_max_shift.assign(size_t(t.n_dtiles), 0);
     for (int k = 0; k < t.n_dtiles; ++k) {
         const int d0 = k * t.Dt, d1 = std::min(p->D, d0 + t.Dt);
         for (int c0 = 0; c0 < p->C; c0 += cch) {
@@ -163,6 +164,7 @@ dd_status build_fwd_tables(dd_plan_s *p, const dd_variant &v, FwdTables *out) {
                     smin = std::min(smin, sh);
                     smax = std::max(smax, sh);
                 }
+                t.dtile_max_shift[size_t(k)] = std::max(t.dtile_max_shift[size_t(k)], smax);
                 const int64_t ws = floor_to(smin, al);
                 const int64_t len = round_up(smax + t.Ts - ws, al);
                 if (soff + len > 65536) return fail(DD_ERR_ARG, "stage too large for variant");
