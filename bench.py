@@ -15,8 +15,9 @@ the C ABI's dd_execute. Prints ONE JSON line (rank 0).
             the brute-force method is bound by arithmetic, not HBM; the HBM
             fraction is reported beside it
   extras    8-bit / FP16 batched forms of the uneven-beam workload against
-            plain FP32 launches of the same workload, the HBM-bound 96-beam
-            FP32 point, and the differentiable workload's forward+backward
+            plain FP32 launches of the same workload, the survey workload in
+            16-bit and 8-bit input, the HBM-bound 96-beam FP32 point, and the
+            differentiable workload's forward, adjoint and forward+backward
 
 --impl reference times the FP64 CPU oracle on a bounded sample of the same
 workload (the paper publishes no code to run).
@@ -60,7 +61,7 @@ def _args():
     ap.add_argument("--no-extras", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--only", choices=["uneven_u8", "uneven_f16", "uneven_f32", "f32_96beams",
-                                       "differentiable"],
+                                       "survey_precisions", "differentiable"],
                     help="run one secondary workload alone (for profiling its kernels)")
     ap.add_argument("--no-tune", action="store_true",
                     help="with --only: keep the plans' starting variants (the built-in default, "
@@ -347,10 +348,39 @@ def _case_differentiable(torch, flush, n_rep, tune=True):
             "variant": p.variant, "adjoint_variant": rep_adj["best"] if rep_adj else None}
 
 
-def _extras(torch, flush, peaks, steps):
+def _case_survey_precisions(torch, flush, n_rep, f32_ms=None):
+    """The survey workload (1 beam x 1024 ch x 2048 DM x 20000) with 16-bit
+    and 8-bit input against FP32, each in its default variant."""
+    import synth
+    from paper_1601_05052_gb300 import Plan
+    g = torch.Generator(device="cuda")
+    s = synth.setup(WORKLOAD)
+    units = s.batch * s.n_dm * s.n_out
+    out = {"workload": "survey scale, default variant per input type", "unit": UNIT}
+    for dtype in ("f32", "f16", "bf16", "u8"):
+        if dtype == "f32" and f32_ms is not None:
+            out["f32"] = units / (f32_ms * 1e-3)
+            continue
+        p = Plan.from_setup(s, dtype=dtype)
+        x = _rand_input(torch, g, p, 11, dtype)
+        w = (torch.full((p.n_chan,), 256, dtype=torch.int32, device="cuda") if dtype == "u8"
+             else torch.ones(p.n_chan, device="cuda"))
+        o = torch.empty(p.out_shape, dtype=p.out_dtype, device="cuda")
+        t = statistics.median(_time_steps(lambda: p.execute(x, w, o), n_rep, 2, flush, torch))
+        out[dtype] = units / (t * 1e-3)
+        out[dtype + "_variant"] = p.variant
+        del x, o
+        p.close()
+    for dtype in ("f16", "bf16", "u8"):
+        out["speedup_%s_vs_f32" % dtype] = out[dtype] / out["f32"]
+    return out
+
+
+def _extras(torch, flush, peaks, steps, f32_ms=None):
     """Secondary measurement points (rank 0, one GPU)."""
     n_rep = max(3, min(20, steps // 10))
     return {"uneven_beams": _case_uneven(torch, flush, n_rep),
+            "survey_precisions": _case_survey_precisions(torch, flush, n_rep, f32_ms),
             "f32_96beams_64ch": _case_96beams(torch, flush, n_rep, peaks),
             "differentiable_16beams": _case_differentiable(torch, flush, n_rep)}
 
@@ -370,6 +400,8 @@ def run_only(args):
                            variant=variant)
     elif args.only == "f32_96beams":
         out = _case_96beams(torch, flush, n, peaks, tune=tune, variant=variant)
+    elif args.only == "survey_precisions":
+        out = _case_survey_precisions(torch, flush, n)
     else:
         out = _case_differentiable(torch, flush, n, tune=tune)
     print(json.dumps({"case": args.only, "steps": n, **out}), flush=True)
@@ -484,7 +516,7 @@ def run_ours(args):
                                  "hd7970_dm_trial_samples_per_s": 2000 * 20000 / 0.106,
                                  "note": "AMD HD7970, OpenCL FP32, 2000 DMs (not 2048): context"}
         if world == 1 and not args.no_extras:
-            line["extras"] = _extras(torch, flush, peaks, args.steps)
+            line["extras"] = _extras(torch, flush, peaks, args.steps, f32_ms=ms)
         if world == 1 and not args.no_cpu_baseline:
             line["cpu_baseline"] = _cpu_baseline(x_host, w_host, sh.astype(np.int64), s)
         print(json.dumps(line), flush=True)
