@@ -48,7 +48,7 @@ KERNEL_SOURCES = ["paper_1601_05052_gb300/csrc/dd_fwd_tile.cuh",
                   "paper_1601_05052_gb300/csrc/dd_kinds.h"]
 TRAFFIC_PROFILE = "profiles/fwd_survey_f32.md"
 UNIT = "DM-trial·samples/s"
-WORKLOAD = "cfg2"
+WORKLOAD = "apertif_survey"
 L2_FLUSH_BYTES = 256 << 20
 
 
@@ -263,7 +263,7 @@ def _case_uneven(torch, flush, n_rep, dtypes=("u8", "f16", "f32"), tune=True, va
     import synth
     from paper_1601_05052_gb300 import Batch, Plan
     g = torch.Generator(device="cuda")
-    hi, lo = synth.setup("cfg4_hi"), synth.setup("cfg4_lo")
+    hi, lo = synth.setup("lband64_x96_u8"), synth.setup("lowfreq256_u8")
     units = hi.batch * hi.n_dm * hi.n_out + lo.batch * lo.n_dm * lo.n_out
     res, used = {}, {}
     for dtype in dtypes:
@@ -298,11 +298,11 @@ def _case_uneven(torch, flush, n_rep, dtypes=("u8", "f16", "f32"), tune=True, va
 
 
 def _case_96beams(torch, flush, n_rep, peaks, tune=True, variant=None):
-    """The cfg1 shape at 96 beams in FP32, the point where HBM could bind."""
+    """The lband64 shape at 96 beams in FP32, the point where HBM could bind."""
     import synth
     from paper_1601_05052_gb300 import Plan
     g = torch.Generator(device="cuda")
-    s = synth.setup("cfg1x96")
+    s = synth.setup("lband64_x96")
     p = Plan.from_setup(s)
     if variant:
         p.variant = variant
@@ -323,7 +323,7 @@ def _case_differentiable(torch, flush, n_rep, tune=True):
     import synth
     from paper_1601_05052_gb300 import Plan, dedisperse
     g = torch.Generator(device="cuda")
-    s = synth.setup("cfg5")
+    s = synth.setup("diff16_512ch")
     p = Plan.from_setup(s)
     rep_adj = None
     if tune:

@@ -49,25 +49,26 @@ class Setup:
 
 
 SETUPS = {
-    # 1: plain FP32, one beam, 64 channels over 1400-1500 MHz, 64 us, DMs 0..31.5.
-    "cfg1": Setup("cfg1", 64, 1400.0, 1500.0, 64e-6, 0.0, 0.5, 64, 4096),
-    # 2: survey scale, Apertif-like: 1024 ch over 1420-1720 MHz, 50 us, 2048 DMs step 0.25.
-    "cfg2": Setup("cfg2", 1024, 1420.0, 1720.0, 50e-6, 0.0, 0.25, 2048, 20000),
-    # 3: the precision forms of cfg1 (u8 / f16 / bf16 inputs, weighted).
-    "cfg3_u8": Setup("cfg3_u8", 64, 1400.0, 1500.0, 64e-6, 0.0, 0.5, 64, 4096, dtype="u8"),
-    "cfg3_f16": Setup("cfg3_f16", 64, 1400.0, 1500.0, 64e-6, 0.0, 0.5, 64, 4096, dtype="f16"),
-    "cfg3_bf16": Setup("cfg3_bf16", 64, 1400.0, 1500.0, 64e-6, 0.0, 0.5, 64, 4096, dtype="bf16"),
-    # 4: batched uneven beams: 96 beams of the cfg1 shape plus 32 low-frequency beams.
-    "cfg4_hi": Setup("cfg4_hi", 64, 1400.0, 1500.0, 64e-6, 0.0, 0.5, 64, 4096, batch=96, dtype="u8"),
-    "cfg4_lo": Setup("cfg4_lo", 256, 120.0, 180.0, 204.8e-6, 0.0, 0.05, 2000, 10000, batch=32, dtype="u8"),
-    # 5: differentiable weighted dedispersion, 16 beams.
-    "cfg5": Setup("cfg5", 512, 1250.0, 1550.0, 100e-6, 0.0, 0.25, 1024, 8192, batch=16),
-    # extra measurement point: the cfg1 shape at 96 beams in FP32 (leaves L2).
-    "cfg1x96": Setup("cfg1x96", 64, 1400.0, 1500.0, 64e-6, 0.0, 0.5, 64, 4096, batch=96),
+    # plain FP32, one beam, 64 channels over 1400-1500 MHz, 64 us, DMs 0..31.5.
+    "lband64": Setup("lband64", 64, 1400.0, 1500.0, 64e-6, 0.0, 0.5, 64, 4096),
+    # survey scale, Apertif-like: 1024 ch over 1420-1720 MHz, 50 us, 2048 DMs step 0.25.
+    "apertif_survey": Setup("apertif_survey", 1024, 1420.0, 1720.0, 50e-6, 0.0, 0.25, 2048, 20000),
+    # the precision forms of lband64 (u8 / f16 / bf16 inputs, weighted).
+    "lband64_u8": Setup("lband64_u8", 64, 1400.0, 1500.0, 64e-6, 0.0, 0.5, 64, 4096, dtype="u8"),
+    "lband64_f16": Setup("lband64_f16", 64, 1400.0, 1500.0, 64e-6, 0.0, 0.5, 64, 4096, dtype="f16"),
+    "lband64_bf16": Setup("lband64_bf16", 64, 1400.0, 1500.0, 64e-6, 0.0, 0.5, 64, 4096, dtype="bf16"),
+    # batched uneven beams: 96 beams of the lband64 shape plus 32 low-frequency beams
+    # (256 ch over 120-180 MHz, 204.8 us, 2000 DMs step 0.05).
+    "lband64_x96_u8": Setup("lband64_x96_u8", 64, 1400.0, 1500.0, 64e-6, 0.0, 0.5, 64, 4096, batch=96, dtype="u8"),
+    "lowfreq256_u8": Setup("lowfreq256_u8", 256, 120.0, 180.0, 204.8e-6, 0.0, 0.05, 2000, 10000, batch=32, dtype="u8"),
+    # differentiable weighted dedispersion, 16 beams of 512 ch over 1250-1550 MHz.
+    "diff16_512ch": Setup("diff16_512ch", 512, 1250.0, 1550.0, 100e-6, 0.0, 0.25, 1024, 8192, batch=16),
+    # extra measurement point: the lband64 shape at 96 beams in FP32 (leaves L2).
+    "lband64_x96": Setup("lband64_x96", 64, 1400.0, 1500.0, 64e-6, 0.0, 0.5, 64, 4096, batch=96),
     # the paper's LOFAR-like setup (32 ch x 0.1953125 MHz from 138 MHz, 5 us).
     "lofar": Setup("lofar", 32, 138.0, 138.0 + 32 * 0.1953125, 5e-6, 0.0, 0.25, 2048, 200000),
     # Apertif DM = 0 "perfect reuse" form (all trial DMs zero).
-    "cfg2_dm0": Setup("cfg2_dm0", 1024, 1420.0, 1720.0, 50e-6, 0.0, 0.0, 2048, 20000),
+    "apertif_survey_dm0": Setup("apertif_survey_dm0", 1024, 1420.0, 1720.0, 50e-6, 0.0, 0.0, 2048, 20000),
 }
 
 

@@ -117,12 +117,12 @@ def test_autograd_function_backward():
     assert_float_parity(wt.grad.cpu().numpy(), ref_gw, abw, what="autograd grad_w")
 
 
-def test_workload5_finite_differences():
+def test_16beam_512ch_1024dm_finite_differences():
     """Loss = sum of out^2 over trials [256, 768) x samples [2048, 6144) of all
     16 beams; 32 input and 32 weight coordinates against FP64 central
     differences (h = 1e-3) of the oracle's loss restricted to the outputs each
     perturbation touches (exact for a quadratic loss)."""
-    s = synth.setup("cfg5")
+    s = synth.setup("diff16_512ch")
     sh = oracle.shift_table(s.freqs(), s.f_ref, s.t_samp, s.dms())
     pulses = synth.pulse_plan(s, 5)
     x = synth.make_input(s, sh, seed=5, pulses=pulses, pad_value=np.float32(0))

@@ -41,12 +41,12 @@ def test_small_uneven_batch_full(dtype):
         p.check_device()
 
 
-def test_batched_uneven_beams_u8_workload4_sampled():
+def test_batched_96_plus_32_uneven_beams_u8_sampled():
     """96 beams of the 64-channel setup plus 32 low-frequency beams (256 ch
     over 120-180 MHz, 2000 trials, 10000 samples), 8-bit input, unit weights,
     one persistent launch: sampled outputs bit-exact, and the tuned batch
     variant stays exact."""
-    hi, lo = synth.setup("cfg4_hi"), synth.setup("cfg4_lo")
+    hi, lo = synth.setup("lband64_x96_u8"), synth.setup("lowfreq256_u8")
     plans, data = [], []
     for s, seed in ((hi, 41), (lo, 42)):
         sh = oracle.shift_table(s.freqs(), s.f_ref, s.t_samp, s.dms())

@@ -27,24 +27,24 @@ def _setup_case(name, dtype, wkind, seed):
     return s, sh, x, w
 
 
-def test_workload1_plain_f32_full():
+def test_64ch_64dm_4096_plain_f32_full():
     """64 channels, 64 trials, 4096 samples, FP32, unit weights, one pulse."""
-    s, sh, x, w = _setup_case("cfg1", "f32", "ones", 1)
+    s, sh, x, w = _setup_case("lband64", "f32", "ones", 1)
     plan = Plan.from_setup(s)
     np.testing.assert_array_equal(plan.shifts(), sh)
-    out = check_full(plan, x, w, sh, "f32", "cfg1")
+    out = check_full(plan, x, w, sh, "f32", "lband64")
     d, t = np.unravel_index(np.argmax(out[0]), out[0].shape)
     assert t == 1000 and abs(int(d) - 40) <= 1
     plan.check_device()
 
 
 @pytest.mark.parametrize("dtype", ["u8", "f16", "bf16"])
-def test_workload3_precision_forms_full(dtype):
+def test_64ch_64dm_4096_precision_forms_full(dtype):
     """Workload 1's shapes and pulse with weights U(0.5,1.5), 5% masked:
     u8 bit-exact (int32), f16/bf16 within 1e-4 * sum|w*in|."""
-    s, sh, x, w = _setup_case("cfg3_" + dtype, dtype, "uniform", 3)
+    s, sh, x, w = _setup_case("lband64_" + dtype, dtype, "uniform", 3)
     plan = Plan.from_setup(s)
-    check_full(plan, x, w, sh, dtype, "cfg3 " + dtype)
+    check_full(plan, x, w, sh, dtype, "lband64 " + dtype)
     plan.check_device()
 
 
@@ -308,7 +308,7 @@ def test_survey_scale_f32_sampled():
     """The benchmark workload (1024 ch, 2048 trials, 20000 samples, FP32) in
     the launch configuration the benchmark times: sampled outputs, plus the
     ten injected pulses."""
-    s = synth.setup("cfg2")
+    s = synth.setup("apertif_survey")
     sh = oracle.shift_table(s.freqs(), s.f_ref, s.t_samp, s.dms())
     pulses = synth.pulse_plan(s, 2, n_per_beam=10)
     x = synth.make_input(s, sh, seed=2, pulses=pulses)
@@ -325,7 +325,7 @@ def test_survey_scale_f32_sampled():
     pb = np.zeros_like(pd)
     ref, ab = oracle.forward_points(x, w, sh, pb, pd, pt)
     got = out[0][torch.from_numpy(pd).cuda(), torch.from_numpy(pt).cuda()].cpu().numpy()
-    assert_float_parity(got, ref, ab, what="cfg2 sampled")
+    assert_float_parity(got, ref, ab, what="apertif_survey sampled")
     # each pulse is recovered at its own trial and time
     for (_, d, t0, a) in pulses:
         col = out[0, :, t0].cpu().numpy()

@@ -30,7 +30,7 @@ def test_shift_hand_worked_cases():
         assert got.tolist() == case["expected"], case["_derivation"]
 
 
-@pytest.mark.parametrize("name", ["cfg1", "cfg2", "cfg5", "cfg4_lo", "lofar"])
+@pytest.mark.parametrize("name", ["lband64", "apertif_survey", "diff16_512ch", "lowfreq256_u8", "lofar"])
 def test_shift_table_structure(name):
     s = synth.setup(name)
     sh = oracle.shift_table(s.freqs(), s.f_ref, s.t_samp, s.dms())
@@ -45,7 +45,7 @@ def test_shift_scale_matches_paper_constant():
     """Eq. 1 with the paper's printed K ~ 4150 agrees to K's precision
     (0.029 %) plus one rounding step: pins units (MHz, seconds) and the
     inverse-square law's scale."""
-    s = synth.setup("cfg2")
+    s = synth.setup("apertif_survey")
     f, fr, ts, dm = s.freqs(), s.f_ref, s.t_samp, s.dms()
     sh = oracle.shift_table(f, fr, ts, dm)
     approx = K_PAPER * dm[:, None] * (1 / f[None, :] ** 2 - 1 / fr ** 2) / ts
@@ -54,7 +54,7 @@ def test_shift_scale_matches_paper_constant():
 
 
 def test_shift_linear_in_dm_and_inverse_in_tsamp():
-    s = synth.setup("cfg5")
+    s = synth.setup("diff16_512ch")
     f, fr = s.freqs(), s.f_ref
     dm = np.array([10.0, 20.0, 40.0])
     a = oracle.shift_table(f, fr, 1e-4, dm)
@@ -81,7 +81,7 @@ def test_shift_rejects_negative_and_bad_args():
 def test_paper_flop_count_per_dm():
     """Section IV: the Apertif setup is 20 MFLOP per DM, LOFAR 6 MFLOP per DM
     (one addition per channel per output sample)."""
-    ap, lo = synth.setup("cfg2"), synth.setup("lofar")
+    ap, lo = synth.setup("apertif_survey"), synth.setup("lofar")
     assert ap.n_out * ap.n_chan == 20_480_000
     assert lo.n_out * lo.n_chan == 6_400_000
 
@@ -134,7 +134,7 @@ def test_forward_brute_force_python_loops():
 def test_forward_dm0_is_weighted_channel_sum():
     """Section IV-C: with every trial DM equal to 0 there are no shifts and
     every output row is the (weighted) channel sum."""
-    s = synth.setup("cfg1")
+    s = synth.setup("lband64")
     sh = oracle.shift_table(s.freqs(), s.f_ref, s.t_samp, np.zeros(8))
     rng = np.random.default_rng(3)
     x = rng.standard_normal((1, s.n_chan, 512)).astype(np.float32)
@@ -146,7 +146,7 @@ def test_forward_dm0_is_weighted_channel_sum():
 
 
 def test_forward_constant_and_ramp_closed_forms():
-    s = synth.setup("cfg1")
+    s = synth.setup("lband64")
     sh = oracle.shift_table(s.freqs(), s.f_ref, s.t_samp, s.dms())
     S = 300
     T = S + int(sh.max())
@@ -165,7 +165,7 @@ def test_forward_dispersed_impulse_peaks_at_its_trial():
     """A unit impulse dispersed along trial d* sums to sum_c w_c exactly at
     (d*, t0); any other trial reaching that value must share d*'s shift column
     on every weighted channel."""
-    s = synth.setup("cfg1")
+    s = synth.setup("lband64")
     sh = oracle.shift_table(s.freqs(), s.f_ref, s.t_samp, s.dms())
     S, dstar, t0 = 2048, 40, 1000
     T = S + int(sh.max())
@@ -297,7 +297,7 @@ def test_grad_w_central_difference():
 def test_input_recipe_places_pulses_on_the_trial():
     """The synthetic recipe: a pulse added along trial d* dominates trial d*
     at t0 (noise N(0,1), amplitude 5, 64 channels)."""
-    s = synth.setup("cfg1")
+    s = synth.setup("lband64")
     sh = oracle.shift_table(s.freqs(), s.f_ref, s.t_samp, s.dms())
     pulses = synth.pulse_plan(s, 1, fixed=(40, 1000, 5.0))
     x = synth.make_input(s, sh, seed=1, pulses=pulses)
