@@ -494,7 +494,14 @@ def run_ours(args):
                                  "frac": eff_gbs / peaks["hbm_gbs"],
                                  "compulsory_bytes": comp_bytes}},
             "gpu_launches": args.steps,
-            "clocks": clocks}
+            "clocks": clocks,
+            # Section V-B's real-time check: seconds of observation per beam
+            # (S samples of t_samp) against the seconds one GPU spends on them
+            "real_time": {"seconds_of_data": s.n_out * s.t_samp,
+                          "seconds_to_dedisperse": ms * 1e-3 / s.batch,
+                          "factor": s.n_out * s.t_samp / (ms * 1e-3 / s.batch)},
+            # the paper's flop count: one add per channel per output (Section IV)
+            "paper_gflops": ops / (ms * 1e-3) / 1e9}
     if tune_rep:
         line["tune"] = tune_rep
 
