@@ -1,0 +1,49 @@
+"""Host-side logic of the benchmark and the experiment report, on CPU: the
+DRAM traffic recorded in the committed ncu summary is reported only for the
+kernel sources and variant it was taken from, and the tuning-experiment table
+is rendered from the run's own results."""
+import json
+import os
+import sys
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import bench  # noqa: E402
+from paper_1601_05052_gb300 import experiments  # noqa: E402
+
+
+def _profile_variant():
+    text = open(os.path.join(ROOT, bench.TRAFFIC_PROFILE)).read()
+    line = next(l for l in text.splitlines() if l.startswith("variant: "))
+    return json.loads(line[len("variant: "):])
+
+
+def test_recorded_traffic_matches_sources_and_variant():
+    v = _profile_variant()
+    t = bench.recorded_traffic(v)
+    assert t is not None and 1e8 < t < 3e8  # read + write bytes of one survey launch
+    other = dict(v, stages=v["stages"] + 1)
+    assert bench.recorded_traffic(other) is None
+
+
+def test_kernel_hash_is_stable_and_covers_the_sources():
+    assert bench.kernel_hash() == bench.kernel_hash()
+    assert len(bench.kernel_hash()) == 16
+    for f in bench.KERNEL_SOURCES:
+        assert os.path.exists(os.path.join(ROOT, f)), f
+
+
+def test_experiment_table_rendering():
+    rows = lambda vals: [{"n_dm": n, "best_gflops": g, "mean_gflops": g / 2, "snr": 2.0,
+                          "chebyshev": 0.25, "speedup_tuned_over_fixed": 1.1}
+                         for n, g in vals]
+    res = [{"setup": "apertif", "dm0_only": False, "instances": rows([(2, 100.0), (4, 210.4)])},
+           {"setup": "apertif", "dm0_only": True, "instances": rows([(2, 120.0)])},
+           {"setup": "lofar", "dm0_only": False, "instances": rows([(4, 50.0)])}]
+    md = experiments.markdown(res).splitlines()
+    assert md[0].startswith("| D | Apertif best GFLOP/s")
+    assert md[2] == "| 2 | 100 | 50 | 2.00 | 0.25 | 1.10 | 120 | - | - |"
+    assert md[3] == "| 4 | 210 | 105 | 2.00 | 0.25 | 1.10 | - | 50 | - |"
+    assert len(md) == 4
