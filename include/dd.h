@@ -32,8 +32,10 @@
  *   - Errors. Every call returns a dd_status; the last failure's message is
  *     kept per thread (dd_last_error_message). No call throws or aborts.
  *   - Threads. A plan may be used from several threads and streams at once
- *     for dd_execute / dd_adjoint; dd_tune and dd_plan_set_variant must not
- *     run concurrently with other calls on the same plan.
+ *     for dd_execute. dd_adjoint and dd_execute_host use plan-owned device
+ *     buffers, so their calls on one plan must be ordered (one stream, one
+ *     thread at a time); dd_tune, dd_tune_adjoint and the set_variant calls
+ *     must not run concurrently with other calls on the same plan.
  */
 #ifndef DD_H_
 #define DD_H_
@@ -164,7 +166,9 @@ dd_status dd_execute(dd_plan plan, const void *d_in, const void *d_w, void *d_ou
  * CPU-GPU link, and the input is pulled in up to 8 segments of whole time
  * tiles: segment s's forward launch starts as soon as the columns it needs
  * (its samples plus the max delay) are on the device, while later columns are
- * still in flight (plan-owned copy and compute streams, joined to `stream`).
+ * still in flight, and the first segment's low-DM tiles start once the
+ * columns of their own largest delay are in (plan-owned copy and compute
+ * streams, joined to `stream`).
  * Pageable buffers are staged through plan-owned device mirrors. Not safe to
  * call concurrently on one plan. */
 dd_status dd_execute_host(dd_plan plan, const void *h_in, const void *h_w, void *h_out,
