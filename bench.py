@@ -61,7 +61,7 @@ def _args():
     ap.add_argument("--no-extras", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--only", choices=["uneven_u8", "uneven_f16", "uneven_f32", "f32_96beams",
-                                       "survey_precisions", "differentiable"],
+                                       "f32_hbm_bound", "survey_precisions", "differentiable"],
                     help="run one secondary workload alone (for profiling its kernels)")
     ap.add_argument("--no-tune", action="store_true",
                     help="with --only: keep the plans' starting variants (the built-in default, "
@@ -297,12 +297,14 @@ def _case_uneven(torch, flush, n_rep, dtypes=("u8", "f16", "f32"), tune=True, va
     return out
 
 
-def _case_96beams(torch, flush, n_rep, peaks, tune=True, variant=None):
-    """The lband64 shape at 96 beams in FP32, the point where HBM could bind."""
+def _case_96beams(torch, flush, n_rep, peaks, tune=True, variant=None, name="lband64_x96"):
+    """A 64-channel setup over many beams in FP32: the benchmark's 96-beam
+    point (where HBM could bind), or the 4-trial, 384-beam point where it
+    does."""
     import synth
     from paper_1601_05052_gb300 import Plan
     g = torch.Generator(device="cuda")
-    s = synth.setup("lband64_x96")
+    s = synth.setup(name)
     p = Plan.from_setup(s)
     if variant:
         p.variant = variant
@@ -382,6 +384,8 @@ def _extras(torch, flush, peaks, steps, f32_ms=None):
     return {"uneven_beams": _case_uneven(torch, flush, n_rep),
             "survey_precisions": _case_survey_precisions(torch, flush, n_rep, f32_ms),
             "f32_96beams_64ch": _case_96beams(torch, flush, n_rep, peaks),
+            "f32_hbm_bound_4dm_384beams": _case_96beams(torch, flush, n_rep, peaks,
+                                                        name="lband64_4dm_x384"),
             "differentiable_16beams": _case_differentiable(torch, flush, n_rep)}
 
 
@@ -400,6 +404,9 @@ def run_only(args):
                            variant=variant)
     elif args.only == "f32_96beams":
         out = _case_96beams(torch, flush, n, peaks, tune=tune, variant=variant)
+    elif args.only == "f32_hbm_bound":
+        out = _case_96beams(torch, flush, n, peaks, tune=tune, variant=variant,
+                            name="lband64_4dm_x384")
     elif args.only == "survey_precisions":
         out = _case_survey_precisions(torch, flush, n)
     else:

@@ -65,6 +65,10 @@ SETUPS = {
     "diff16_512ch": Setup("diff16_512ch", 512, 1250.0, 1550.0, 100e-6, 0.0, 0.25, 1024, 8192, batch=16),
     # extra measurement point: the lband64 shape at 96 beams in FP32 (leaves L2).
     "lband64_x96": Setup("lband64_x96", 64, 1400.0, 1500.0, 64e-6, 0.0, 0.5, 64, 4096, batch=96),
+    # an HBM-bound point: the lband64 band with only 4 trial DMs (0-1.5) over 384 beams
+    # (~0.6 adds per compulsory byte, far below the FP32 ridge).
+    "lband64_4dm_x384": Setup("lband64_4dm_x384", 64, 1400.0, 1500.0, 64e-6, 0.0, 0.5, 4, 4096,
+                              batch=384),
     # the paper's LOFAR-like setup (32 ch x 0.1953125 MHz from 138 MHz, 5 us).
     "lofar": Setup("lofar", 32, 138.0, 138.0 + 32 * 0.1953125, 5e-6, 0.0, 0.25, 2048, 200000),
     # Apertif DM = 0 "perfect reuse" form (all trial DMs zero).
