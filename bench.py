@@ -15,9 +15,12 @@ the C ABI's dd_execute. Prints ONE JSON line (rank 0).
             the brute-force method is bound by arithmetic, not HBM; the HBM
             fraction is reported beside it
   extras    8-bit / FP16 batched forms of the uneven-beam workload against
-            plain FP32 launches of the same workload, the survey workload in
-            16-bit and 8-bit input, the HBM-bound 96-beam FP32 point, and the
-            differentiable workload's forward, adjoint and forward+backward
+            plain FP32 launches of the same workload (default and per-plan
+            tuned), the survey workload in 16-bit and 8-bit input, the
+            64-channel workload and its 8/16-bit forms as graph-replayed
+            microsecond launches (L2-resident) beside the FP64 oracle, the
+            96-beam and HBM-bound FP32 points, and the differentiable
+            workload's forward, adjoint and forward+backward
 
 --impl reference times the FP64 CPU oracle on a bounded sample of the same
 workload (the paper publishes no code to run).
@@ -61,7 +64,8 @@ def _args():
     ap.add_argument("--no-extras", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--only", choices=["uneven_u8", "uneven_f16", "uneven_f32", "f32_96beams",
-                                       "f32_hbm_bound", "survey_precisions", "differentiable"],
+                                       "f32_hbm_bound", "survey_precisions", "differentiable",
+                                       "small_graph"],
                     help="run one secondary workload alone (for profiling its kernels)")
     ap.add_argument("--no-tune", action="store_true",
                     help="with --only: keep the plans' starting variants (the built-in default, "
@@ -90,13 +94,15 @@ def kernel_hash():
     return h.hexdigest()[:16]
 
 
-def recorded_traffic(variant):
+def recorded_traffic(variant, text=None):
     """DRAM bytes per launch of the forward kernel from the committed ncu
-    summary, or None if the kernel sources or the variant changed since."""
-    try:
-        text = open(os.path.join(ROOT, TRAFFIC_PROFILE)).read()
-    except OSError:
-        return None
+    summary (or `text`), or None if the kernel sources or the variant changed
+    since."""
+    if text is None:
+        try:
+            text = open(os.path.join(ROOT, TRAFFIC_PROFILE)).read()
+        except OSError:
+            return None
     m_hash = re.search(r"kernel source hash: ([0-9a-f]{16})", text)
     m_var = re.search(r"variant: (\{[^}]*\})", text)
     m_rd = re.search(r"dram__bytes_read\.sum: ([0-9.]+) MB", text)
@@ -262,7 +268,10 @@ def _rand_input(torch, g, p, seed, dtype):
 
 def _case_uneven(torch, flush, n_rep, dtypes=("u8", "f16", "f32"), tune=True, variant=None):
     """Uneven-beam batch: 96 x (64 ch) + 32 x (256 ch, low frequency); 8-bit
-    and FP16 as one graph-captured persistent launch, FP32 as plain launches."""
+    and FP16 as one graph-captured persistent launch (batch-tuned), FP32 as
+    plain launches, once in each plan's default variant and once with each
+    plan tuned on its own (the like-for-like comparison: tuned against
+    tuned)."""
     import synth
     from paper_1601_05052_gb300 import Batch, Plan
     g = torch.Generator(device="cuda")
@@ -276,6 +285,15 @@ def _case_uneven(torch, flush, n_rep, dtypes=("u8", "f16", "f32"), tune=True, va
         outs = [torch.empty(p.out_shape, dtype=p.out_dtype, device="cuda") for p in plans]
         if dtype == "f32":  # the plain form: one dd_execute launch per setup
             fn = lambda: [p.execute(x, w, o) for p, x, w, o in zip(plans, xs, ws, outs)]
+            used["f32_default"] = [p.variant for p in plans]
+            res["f32_default"] = units / (statistics.median(
+                _time_steps(fn, n_rep, 2, flush, torch)) * 1e-3)
+            if not tune:
+                res[dtype] = res["f32_default"]
+                used[dtype] = used["f32_default"]
+                continue
+            for p in plans:
+                p.tune(budget_ms=8000)
             used[dtype] = [p.variant for p in plans]
         else:
             bt = Batch(plans)
@@ -292,11 +310,64 @@ def _case_uneven(torch, flush, n_rep, dtypes=("u8", "f16", "f32"), tune=True, va
     out = {"workload": "96 beams x (64 ch, 64 DM, 4096 samples) + 32 beams x (256 ch 120-180 "
                        "MHz, 2000 DM, 10000 samples)", "unit": UNIT, "variants": used}
     for dtype in dtypes:
-        out["plain_f32_launches" if dtype == "f32" else "batched_%s_graph" % dtype] = res[dtype]
+        out["plain_f32_tuned_launches" if dtype == "f32" else "batched_%s_graph" % dtype] = \
+            res[dtype]
     if "f32" in res:
+        out["plain_f32_default_launches"] = res["f32_default"]
         for dtype in dtypes:
             if dtype != "f32":
                 out["speedup_%s_vs_f32" % dtype] = res[dtype] / res["f32"]
+                out["speedup_%s_vs_f32_default" % dtype] = res[dtype] / res["f32_default"]
+    return out
+
+
+def _case_small_graph(torch, n_rep, per_graph=200):
+    """The 64-channel, 64-trial, 4096-sample workload in FP32 (unit weights)
+    and its 8-bit / FP16 / BF16 forms (weights U(0.5, 1.5), 5 % masked, Q8
+    integers for 8-bit input): a microsecond-scale launch, so `per_graph`
+    launches are captured in one CUDA graph and each step replays it. The
+    1.1 MB input and 1 MB output stay in L2 across launches (L2-resident, no
+    flush). Beside it, the FP64 oracle on the same input."""
+    import oracle
+    import synth
+    from paper_1601_05052_gb300 import Plan
+    out = {"workload": "64 ch (1400-1500 MHz, 64 us) x 64 DM (0-31.5) x 4096 samples, 1 beam",
+           "unit": UNIT, "launches_per_graph": per_graph,
+           "l2": "L2-resident (input and output stay in L2 across the replayed launches)"}
+    for dtype in ("f32", "u8", "f16", "bf16"):
+        s = synth.setup("lband64" if dtype == "f32" else "lband64_" + dtype)
+        sh = oracle.shift_table(s.freqs(), s.f_ref, s.t_samp, s.dms())
+        pulses = synth.pulse_plan(s, 1, fixed=(40, 1000, 5.0))
+        x = synth.make_input(s, sh, seed=1 if dtype == "f32" else 3, pulses=pulses,
+                             pad_value={"u8": np.uint8(0), "bf16": np.uint16(0)}.get(dtype, 0))
+        w = synth.make_weights(s.n_chan, 3, "ones" if dtype == "f32" else "uniform")
+        if dtype == "u8":
+            w = synth.quantize_weights_q8(w)
+        p = Plan.from_setup(s)
+        xt = torch.from_numpy(x)
+        if dtype == "bf16":
+            xt = xt.view(torch.bfloat16)
+        xd = xt.cuda()
+        wd = torch.from_numpy(np.ascontiguousarray(w)).cuda()
+        od = torch.empty(p.out_shape, dtype=p.out_dtype, device="cuda")
+        p.execute(xd, wd, od)  # first launch outside the capture
+        torch.cuda.synchronize()
+        graph = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(graph):
+            for _ in range(per_graph):
+                p.execute(xd, wd, od)
+        t = statistics.median(_time_steps(graph.replay, n_rep, 3, None, torch)) / per_graph
+        t0 = time.perf_counter()
+        if dtype == "u8":
+            oracle.forward_u8(x, w, sh, s.n_out)
+        else:
+            oracle.forward(x, w, sh, s.n_out, dtype=dtype)
+        t_or = time.perf_counter() - t0
+        units = s.batch * s.n_dm * s.n_out
+        out[dtype] = {"value": units / (t * 1e-3), "us_per_launch": t * 1e3,
+                      "variant": p.variant, "oracle_ms": t_or * 1e3,
+                      "oracle_value": units / t_or}
+        del graph
     return out
 
 
@@ -387,13 +458,22 @@ def _case_survey_precisions(torch, flush, n_rep, f32_ms=None):
     return out
 
 
+# The HBM-bound point runs this variant (the tuner's usual pick there), so
+# that its DRAM counters in profiles/fwd_hbm_bound_4dm_f32.md belong to the
+# kernel it times.
+HBM_BOUND_VARIANT = {"kind": 0, "dm_per_thread": 4, "samples_per_thread": 8, "warps_dm": 1,
+                     "warps_time": 8, "chans_per_stage": 4, "stages": 3}
+
+
 def _extras(torch, flush, peaks, steps, f32_ms=None):
     """Secondary measurement points (rank 0, one GPU)."""
     n_rep = max(3, min(20, steps // 10))
     return {"uneven_beams": _case_uneven(torch, flush, n_rep),
             "survey_precisions": _case_survey_precisions(torch, flush, n_rep, f32_ms),
+            "small_graph_64ch": _case_small_graph(torch, n_rep),
             "f32_96beams_64ch": _case_96beams(torch, flush, n_rep, peaks),
             "f32_hbm_bound_4dm_384beams": _case_96beams(torch, flush, n_rep, peaks,
+                                                        variant=HBM_BOUND_VARIANT,
                                                         name="lband64_4dm_x384"),
             "differentiable_16beams": _case_differentiable(torch, flush, n_rep)}
 
@@ -414,8 +494,11 @@ def run_only(args):
     elif args.only == "f32_96beams":
         out = _case_96beams(torch, flush, n, peaks, tune=tune, variant=variant)
     elif args.only == "f32_hbm_bound":
-        out = _case_96beams(torch, flush, n, peaks, tune=tune, variant=variant,
+        out = _case_96beams(torch, flush, n, peaks, tune=tune,
+                            variant=variant or HBM_BOUND_VARIANT,
                             name="lband64_4dm_x384")
+    elif args.only == "small_graph":
+        out = _case_small_graph(torch, n)
     elif args.only == "survey_precisions":
         out = _case_survey_precisions(torch, flush, n)
     else:

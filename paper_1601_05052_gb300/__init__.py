@@ -170,11 +170,24 @@ class Plan:
     def _check_in(self, x, w):
         if not (x.is_cuda and w.is_cuda):
             raise ValueError("inputs must be CUDA tensors (no CPU path)")
+        if w.device != x.device:
+            raise ValueError("input and weights must be on one device")
         if tuple(x.shape) != self.in_shape or x.dtype != self.torch_dtype or not x.is_contiguous():
             raise ValueError("input must be contiguous %s %s, got %s %s"
                              % (self.in_shape, self.torch_dtype, tuple(x.shape), x.dtype))
         if tuple(w.shape) != (self.n_chan,) or w.dtype != self.w_dtype or not w.is_contiguous():
             raise ValueError("weights must be contiguous [%d] %s" % (self.n_chan, self.w_dtype))
+
+    @staticmethod
+    def _check_buf(t, shape, dtype, device, what):
+        """A caller-supplied device buffer: its pointer goes to a kernel as is,
+        so it must be a contiguous CUDA tensor of the exact shape and type on
+        the input's device."""
+        if not isinstance(t, torch.Tensor) or not t.is_cuda or t.device != device:
+            raise ValueError("%s must be a CUDA tensor on %s" % (what, device))
+        if tuple(t.shape) != tuple(shape) or t.dtype != dtype or not t.is_contiguous():
+            raise ValueError("%s must be contiguous %s %s, got %s %s"
+                             % (what, tuple(shape), dtype, tuple(t.shape), t.dtype))
 
     def empty_input(self, device="cuda"):
         return torch.empty(self.in_shape, dtype=self.torch_dtype, device=device)
@@ -184,8 +197,8 @@ class Plan:
         self._check_in(x, w)
         if out is None:
             out = torch.empty(self.out_shape, dtype=self.out_dtype, device=x.device)
-        elif tuple(out.shape) != self.out_shape or out.dtype != self.out_dtype:
-            raise ValueError("out must be %s %s" % (self.out_shape, self.out_dtype))
+        else:
+            self._check_buf(out, self.out_shape, self.out_dtype, x.device, "out")
         _lib.check(_lib_().dd_execute(self._h, _ptr(x), _ptr(w), _ptr(out), _stream(stream)))
         return out
 
@@ -205,6 +218,14 @@ class Plan:
         g = g.contiguous()
         if tuple(g.shape) != self.out_shape or g.dtype != torch.float32 or not g.is_cuda:
             raise ValueError("cotangent must be CUDA float32 %s" % (self.out_shape,))
+        if need_gin:
+            if w is None:
+                raise ValueError("the input gradient needs the weights")
+            self._check_buf(w, (self.n_chan,), torch.float32, g.device, "w")
+        if need_gw:
+            if x is None:
+                raise ValueError("the weight gradient needs the input")
+            self._check_buf(x, self.in_shape, torch.float32, g.device, "x")
         gin = torch.empty(self.in_shape, dtype=torch.float32, device=g.device) if need_gin else None
         gw = torch.empty(self.n_chan, dtype=torch.float32, device=g.device) if need_gw else None
         _lib.check(_lib_().dd_adjoint(self._h, _ptr(g), _ptr(w), _ptr(x), _ptr(gin), _ptr(gw),
@@ -286,11 +307,16 @@ class Batch:
 
     def execute(self, xs, ws, outs=None, stream=None):
         n = len(self.plans)
+        if len(xs) != n or len(ws) != n or (outs is not None and len(outs) != n):
+            raise ValueError("one input, weight vector and output per plan (%d)" % n)
+        for p, x, w in zip(self.plans, xs, ws):
+            p._check_in(x, w)
         if outs is None:
             outs = [torch.empty(p.out_shape, dtype=p.out_dtype, device=x.device)
                     for p, x in zip(self.plans, xs)]
-        for p, x, w in zip(self.plans, xs, ws):
-            p._check_in(x, w)
+        else:
+            for i, (p, x, o) in enumerate(zip(self.plans, xs, outs)):
+                Plan._check_buf(o, p.out_shape, p.out_dtype, x.device, "outs[%d]" % i)
         A = ctypes.c_void_p * n
         _lib.check(_lib_().dd_batch_execute(
             self._h, A(*[x.data_ptr() for x in xs]), A(*[w.data_ptr() for w in ws]),
@@ -331,10 +357,11 @@ class Stream:
         if (tuple(chunk.shape) != shape or chunk.dtype != p.torch_dtype or not chunk.is_cuda
                 or not chunk.is_contiguous()):
             raise ValueError("chunk must be a contiguous CUDA %s %s" % (shape, p.torch_dtype))
-        if tuple(w.shape) != (p.n_chan,) or w.dtype != p.w_dtype or not w.is_cuda:
-            raise ValueError("weights must be CUDA [%d] %s" % (p.n_chan, p.w_dtype))
+        p._check_buf(w, (p.n_chan,), p.w_dtype, chunk.device, "weights")
         if out is None:
             out = torch.empty(p.out_shape, dtype=p.out_dtype, device=chunk.device)
+        else:
+            p._check_buf(out, p.out_shape, p.out_dtype, chunk.device, "out")
         _lib.check(_lib_().dd_stream_push(self._h, _ptr(chunk), _ptr(w), _ptr(out),
                                           _stream(stream)))
         return out

@@ -23,11 +23,12 @@
 // S allows), one forward launch writing G into gin (or scratch), and a fused
 // epilogue that scales gin by w and forms each (beam, channel)'s share of
 // grad_w with a fixed-order block reduction; a last kernel adds the beams in
-// a fixed order, so results are bitwise reproducible.
+// FP32 in a fixed order, so results are bitwise reproducible.
 #include <algorithm>
 #include <vector>
 
 #include "dd_internal.h"
+#include "dd_reduce.cuh"
 
 namespace dd {
 
@@ -78,13 +79,11 @@ __global__ void __launch_bounds__(kEpiThreads) dd_adj_epilogue(
     }
 }
 
-// gw[c] = sum over beams of part[b][c], in beam order, in FP64.
+// gw[c] = sum over beams of part[b][c] in FP32, in a fixed order.
 __global__ void dd_gw_reduce_kernel(const float *part, int B, int C, float *gw) {
     const int c = blockIdx.x * blockDim.x + threadIdx.x;
     if (c >= C) return;
-    double s = 0.0;
-    for (int b = 0; b < B; ++b) s += double(part[(long long)b * C + c]);
-    gw[c] = float(s);
+    gw[c] = fixed_order_sum(part + c, B, C);
 }
 
 // g'[row][M + t] = g[row][t] for t < S: block item i copies columns
@@ -160,14 +159,14 @@ dd_status ensure_adj_state(dd_plan_s *p) {
     const dd_plan_s *q = a.plan;
     const size_t gpad_elems = size_t(p->B) * p->D * q->stride;
     cudaError_t e = cudaMalloc(&a.gpad, gpad_elems * sizeof(float));
-    if (e == cudaSuccess) e = cudaMemset(a.gpad, 0, gpad_elems * sizeof(float));
+    if (e == cudaSuccess) e = cudaMemsetAsync(a.gpad, 0, gpad_elems * sizeof(float), q->aux);
     if (e == cudaSuccess) e = cudaMalloc(&a.ones, size_t(p->D) * sizeof(float));
     if (e == cudaSuccess) e = cudaMalloc(&a.part, size_t(p->B) * p->C * sizeof(float));
     if (e == cudaSuccess) {
-        dd_fill_kernel<<<(p->D + 255) / 256, 256>>>(a.ones, p->D, 1.0f);
+        dd_fill_kernel<<<(p->D + 255) / 256, 256, 0, q->aux>>>(a.ones, p->D, 1.0f);
         e = cudaGetLastError();
     }
-    if (e == cudaSuccess) e = cudaDeviceSynchronize();
+    if (e == cudaSuccess) e = cudaStreamSynchronize(q->aux);  // only the set-up work
     if (e != cudaSuccess) {
         free_adj_state(&a);
         return cuda_fail(e, "adjoint buffers");

@@ -41,15 +41,22 @@ template <int KIND, typename T, int DPT, int SPT>
 __global__ void __launch_bounds__(fwd_max_threads(KIND), fwd_min_blocks(KIND, DPT, SPT))
     dd_fwd_persistent_kernel(const BatchArgs ba) {
     extern __shared__ __align__(128) unsigned char smem[];
-    __shared__ long long s_item;
+    // The item number alternates between two words: thread 0 writes the
+    // next one while a warp that is still leaving the previous tile may not
+    // yet have read the current one (a tile with no more chunks than stages
+    // lets the staging warp run ahead of the others).
+    __shared__ long long s_item[2];
     uint64_t *bars = reinterpret_cast<uint64_t *>(smem);
+    const volatile int *gave_up = reinterpret_cast<const volatile int *>(&bars[7]);
     fwd_init_barriers<KIND>(bars, ba.stages);
     uint32_t kbase = 0;
     const long long n_items = ba.item_start[ba.n];
-    for (;;) {
-        if (threadIdx.x == 0) s_item = (long long)atomicAdd(ba.counter, 1ull);
+    for (int it = 0;; it ^= 1) {
+        // a CTA that gave up a wait takes no further items
+        if (threadIdx.x == 0)
+            s_item[it] = *gave_up ? n_items : (long long)atomicAdd(ba.counter, 1ull);
         __syncthreads();
-        const long long item = s_item;
+        const long long item = s_item[it];
         if (item >= n_items) break;
         int i = 0;
         while (item >= ba.item_start[i + 1]) ++i;
@@ -123,18 +130,36 @@ struct dd_batch_s {
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
     bool args_on_device = false;
+    dd::LaunchTracker launches;
+    // tables and graphs replaced after a launch of this batch was captured
+    // into a caller's graph (freed with the batch)
+    std::vector<dd::FwdTables> retired;
+    std::vector<cudaGraphExec_t> retired_exec;
+    std::vector<cudaGraph_t> retired_graph;
 };
 
 namespace dd {
 namespace {
 
-void release_tables(dd_batch_s *bt) {
-    for (auto &t : bt->tabs) free_fwd_tables(&t);
+// Drops the batch's tables and graph once none of its launches can still
+// read them: waits for the batch's own launches only (no device-wide
+// synchronisation); after a capture into a caller's graph they are kept
+// until the batch is destroyed.
+cudaError_t release_tables(dd_batch_s *bt) {
+    const cudaError_t e = bt->launches.wait();
+    if (bt->launches.captured) {
+        bt->retired.insert(bt->retired.end(), bt->tabs.begin(), bt->tabs.end());
+        if (bt->exec) bt->retired_exec.push_back(bt->exec);
+        if (bt->graph) bt->retired_graph.push_back(bt->graph);
+    } else {
+        for (auto &t : bt->tabs) free_fwd_tables(&t);
+        if (bt->exec) cudaGraphExecDestroy(bt->exec);
+        if (bt->graph) cudaGraphDestroy(bt->graph);
+    }
     bt->tabs.clear();
-    if (bt->exec) cudaGraphExecDestroy(bt->exec);
-    if (bt->graph) cudaGraphDestroy(bt->graph);
     bt->exec = nullptr;
     bt->graph = nullptr;
+    return e;
 }
 
 // Per-plan variants can share one persistent launch when they agree on the
@@ -177,7 +202,7 @@ dd_status configure(dd_batch_s *bt, const std::vector<dd_variant> &pv) {
         for (auto &x : tabs) free_fwd_tables(&x);
         return fail(DD_ERR_ARG, "variant does not fit one CTA per SM");
     }
-    release_tables(bt);
+    const cudaError_t we = release_tables(bt);
     bt->tabs = tabs;
     bt->pv = pv;
     bt->smem = smem;
@@ -250,6 +275,7 @@ dd_status configure(dd_batch_s *bt, const std::vector<dd_variant> &pv) {
     }
     if (e == cudaSuccess) e = cudaGraphInstantiate(&bt->exec, bt->graph, 0);
     if (e != cudaSuccess) return cuda_fail(e, "batch graph");
+    if (we != cudaSuccess) return cuda_fail(we, "waiting for the batch's launches");
     return DD_OK;
 }
 
@@ -355,6 +381,7 @@ dd_status dd_batch_execute(dd_batch bt, const void *const *d_in, const void *con
     }
     e = cudaGraphLaunch(bt->exec, st);
     if (e != cudaSuccess) return cuda_fail(e, "cudaGraphLaunch(batch)");
+    bt->launches.note(st);
     return DD_OK;
 }
 
@@ -368,9 +395,7 @@ dd_status dd_batch_set_variant(dd_batch bt, const dd_variant *v) {
     if (!bt || !v) return fail(DD_ERR_ARG, "null argument");
     dd_status s = check_variant_shape(*v);
     if (s != DD_OK) return s;
-    cudaError_t e = cudaDeviceSynchronize();
-    if (e != cudaSuccess) return cuda_fail(e, "cudaDeviceSynchronize");
-    return configure(bt, *v);
+    return configure(bt, *v);  // waits for the batch's own launches before replacing
 }
 
 dd_status dd_batch_get_plan_variant(dd_batch bt, int32_t i, dd_variant *v) {
@@ -391,8 +416,6 @@ dd_status dd_batch_set_plan_variant(dd_batch bt, int32_t i, const dd_variant *v)
         if (!launch_compatible(x, *v))
             return fail(DD_ERR_ARG, "the plans of a batch must share kind, dm_per_thread, "
                                     "samples_per_thread, stages and warps_dm * warps_time");
-    cudaError_t e = cudaDeviceSynchronize();
-    if (e != cudaSuccess) return cuda_fail(e, "cudaDeviceSynchronize");
     const std::vector<dd_variant> old = bt->pv;
     dd_status s = configure(bt, pv);
     if (s != DD_OK) {
@@ -519,7 +542,12 @@ dd_status dd_batch_tune(dd_batch bt, int32_t budget_ms, dd_tune_report *rep) {
 
 void dd_batch_destroy(dd_batch bt) {
     if (!bt) return;
+    bt->launches.captured = false;  // the batch and every graph of its launches end here
     release_tables(bt);
+    for (auto &t : bt->retired) free_fwd_tables(&t);
+    for (cudaGraphExec_t x : bt->retired_exec) cudaGraphExecDestroy(x);
+    for (cudaGraph_t g : bt->retired_graph) cudaGraphDestroy(g);
+    bt->launches.destroy();
     if (bt->d_args) cudaFree(bt->d_args);
     if (bt->d_counter) cudaFree(bt->d_counter);
     delete bt;

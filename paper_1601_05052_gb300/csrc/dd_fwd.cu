@@ -75,16 +75,22 @@ namespace {
 
 using FwdLaunchFn = cudaError_t (*)(const FwdArgs &, dim3, dim3, size_t, cudaStream_t);
 
+constexpr int kMaxDevices = 64;
+
 template <int KIND, typename T, int DPT, int SPT, bool LIVE>
 cudaError_t launch_fwd_t(const FwdArgs &a, dim3 grid, dim3 block, size_t smem, cudaStream_t st) {
-    // Raise the kernel's dynamic shared-memory limit once per size increase.
-    static std::atomic<size_t> smem_set{0};
-    if (smem > 48 * 1024 && smem > smem_set.load()) {
-        cudaError_t e = cudaFuncSetAttribute(dd_fwd_kernel<KIND, T, DPT, SPT, LIVE>,
-                                             cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             int(smem));
+    // Raise the kernel's dynamic shared-memory limit once per size increase
+    // and device (the attribute is set per device).
+    static std::atomic<size_t> smem_set[kMaxDevices];
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    const bool cached = dev >= 0 && dev < kMaxDevices;
+    if (smem > 48 * 1024 && (!cached || smem > smem_set[dev].load())) {
+        e = cudaFuncSetAttribute(dd_fwd_kernel<KIND, T, DPT, SPT, LIVE>,
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
         if (e != cudaSuccess) return e;
-        smem_set.store(smem);
+        if (cached) smem_set[dev].store(smem);
     }
     dd_fwd_kernel<KIND, T, DPT, SPT, LIVE><<<grid, block, smem, st>>>(a);
     return cudaGetLastError();
@@ -170,6 +176,7 @@ dd_status launch_forward(dd_plan_s *p, const FwdTables &t, const void *in, const
     dim3 block(unsigned(32 * (t.v.warps_dm * t.v.warps_time + extra_warps(t.v.kind))));
     cudaError_t e = fn(a, grid, block, t.smem_bytes, st);
     if (e != cudaSuccess) return cuda_fail(e, "forward launch");
+    p->launches.note(st);
     return DD_OK;
 }
 

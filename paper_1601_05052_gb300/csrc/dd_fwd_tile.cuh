@@ -420,6 +420,7 @@ __device__ __forceinline__ void fwd_tile(const FwdArgs &a, int dtile, int ttile,
     using Wt = typename Elem<T>::W;
     uint64_t *full = bars;
     uint64_t *empty = bars + 8;
+    volatile int *gave_up = reinterpret_cast<volatile int *>(&bars[7]);
     const uint32_t S = uint32_t(a.stages);
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int wd = warp % a.warps_dm, wt = warp / a.warps_dm;
@@ -428,12 +429,16 @@ __device__ __forceinline__ void fwd_tile(const FwdArgs &a, int dtile, int ttile,
     const int n_chunks = kr.y - kr.x;
     const Stager<T> st = make_stager<T>(a, dtile, b, t0, stage0, false, kr.x);
 
-    // warp 0 stages chunk k, after the slot's previous chunk was released
+    // warp 0 stages chunk k, after the slot's previous chunk was released;
+    // once the CTA has given up a wait it issues nothing more
     auto issue = [&](int k, int4 dsc) {
         const uint32_t kg = kbase + uint32_t(k);
         const int slot = int(kg % S);
-        if (kg >= S) mbar_wait_bounded(&empty[slot], ((kg / S) - 1u) & 1u, a.err);
-        st.issue(k, slot, dsc, &full[slot], lane);
+        bool ok = true;
+        if (kg >= S)
+            ok = mbar_wait_bounded(&empty[slot], ((kg / S) - 1u) & 1u, a.err, kWaitBudgetNs,
+                                   gave_up);
+        if (__all_sync(0xffffffffu, ok && !*gave_up)) st.issue(k, slot, dsc, &full[slot], lane);
     };
     if (warp == 0) {
         const int pro = min(int(S), n_chunks);
@@ -453,7 +458,12 @@ __device__ __forceinline__ void fwd_tile(const FwdArgs &a, int dtile, int ttile,
         const int kn = k - 1 + int(S);  // the chunk warp 0 stages after this one
         int4 pre = make_int4(0, 0, 0, 0);
         if (warp == 0 && k >= 1 && kn < n_chunks) pre = st.desc(kn, lane);
-        mbar_wait_bounded(&full[slot], (kg / S) & 1u, a.err);
+        // A failed wait (or one that finds the CTA's give-up flag set) ends
+        // the tile: the slot may hold a stale chunk, so nothing more is
+        // summed, released or stored.
+        if (!__all_sync(0xffffffffu, mbar_wait_bounded(&full[slot], (kg / S) & 1u, a.err,
+                                                       kWaitBudgetNs, gave_up)))
+            break;
         const unsigned char *sb = stage0 + slot * st.stage_bytes;
         const T *sdata = reinterpret_cast<const T *>(sb);
         const uint16_t *soffs =
@@ -472,6 +482,7 @@ __device__ __forceinline__ void fwd_tile(const FwdArgs &a, int dtile, int ttile,
         if (warp == 0 && k >= 1 && kn < n_chunks) issue(kn, pre);
     }
     kbase += uint32_t(n_chunks);
+    if (*gave_up) return;
 
     Acc *out = static_cast<Acc *>(a.out);
 #pragma unroll
@@ -725,7 +736,7 @@ __device__ __forceinline__ void fwd_tile_sb(const FwdArgs &a, int dtile, int tti
         sb_trials<Acc, DPT, SPT>(acc, P + lb, poffs + wd * DPT, a.Dt, ng);
     }
     kbase += uint32_t(n_chunks);
-    store_lane_strided<Acc, DPT, SPT>(a, acc, dtile, b, t0, wd, lb);
+    if (!*gave_up) store_lane_strided<Acc, DPT, SPT>(a, acc, dtile, b, t0, wd, lb);
 }
 
 // kind 3: warp-specialised sub-band. Warps [0, NC) are trial warps (as in
@@ -741,6 +752,7 @@ __device__ __forceinline__ void fwd_tile_ws(const FwdArgs &a, int dtile, int tti
     using Acc = typename Elem<T>::Acc;
     using Wt = typename Elem<T>::W;
     uint64_t *full_r = bars, *empty_r = bars + 8, *full_p = bars + 4, *empty_p = bars + 12;
+    volatile int *gave_up = reinterpret_cast<volatile int *>(&bars[7]);
     const uint32_t S = uint32_t(a.stages), Q = uint32_t(kWsPSlots);
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int nc = int(blockDim.x >> 5) - kWsBuilders;  // trial warps
@@ -758,8 +770,12 @@ __device__ __forceinline__ void fwd_tile_ws(const FwdArgs &a, int dtile, int tti
         auto issue = [&](int k, int4 dsc) {  // builder warp 0
             const uint32_t kg = kbase + uint32_t(k);
             const int slot = int(kg % S);
-            if (kg >= S) mbar_wait_bounded(&empty_r[slot], ((kg / S) - 1u) & 1u, a.err);
-            st.issue(k, slot, dsc, &full_r[slot], lane);
+            bool ok = true;
+            if (kg >= S)
+                ok = mbar_wait_bounded(&empty_r[slot], ((kg / S) - 1u) & 1u, a.err, kWaitBudgetNs,
+                                       gave_up);
+            if (__all_sync(0xffffffffu, ok && !*gave_up))
+                st.issue(k, slot, dsc, &full_r[slot], lane);
         };
         if (bw == 0) {
             const int pro = min(int(S), n_chunks);
@@ -771,8 +787,11 @@ __device__ __forceinline__ void fwd_tile_ws(const FwdArgs &a, int dtile, int tti
             const int kn = k - 1 + int(S);
             int4 pre = make_int4(0, 0, 0, 0);
             if (bw == 0 && k >= 1 && kn < n_chunks) pre = st.desc(kn, lane);
-            mbar_wait_bounded(&full_r[rs], (kg / S) & 1u, a.err);
-            if (kg >= Q) mbar_wait_bounded(&empty_p[ps], ((kg / Q) - 1u) & 1u, a.err);
+            bool ok = mbar_wait_bounded(&full_r[rs], (kg / S) & 1u, a.err, kWaitBudgetNs, gave_up);
+            if (ok && kg >= Q)
+                ok = mbar_wait_bounded(&empty_p[ps], ((kg / Q) - 1u) & 1u, a.err, kWaitBudgetNs,
+                                       gave_up);
+            if (!__all_sync(0xffffffffu, ok)) break;  // a lost hand-off ends the tile
             const unsigned char *sb = stage0 + rs * st.stage_bytes;
             const T *raw = reinterpret_cast<const T *>(sb);
             const int4 *bd =
@@ -809,7 +828,9 @@ __device__ __forceinline__ void fwd_tile_ws(const FwdArgs &a, int dtile, int tti
     for (int k = 0; k < n_chunks; ++k) {
         const uint32_t kg = kbase + uint32_t(k);
         const int ps = int(kg % Q);
-        mbar_wait_bounded(&full_p[ps], (kg / Q) & 1u, a.err);
+        if (!__all_sync(0xffffffffu, mbar_wait_bounded(&full_p[ps], (kg / Q) & 1u, a.err,
+                                                       kWaitBudgetNs, gave_up)))
+            break;
         const unsigned char *pb = pslot0 + ps * pslot_bytes;
         const uint16_t *poffs =
             reinterpret_cast<const uint16_t *>(pb + a.p_elems * int(sizeof(Acc))) + wd * DPT;
@@ -819,7 +840,7 @@ __device__ __forceinline__ void fwd_tile_ws(const FwdArgs &a, int dtile, int tti
         if (lane == 0) mbar_arrive(&empty_p[ps]);
     }
     kbase += uint32_t(n_chunks);
-    store_lane_strided<Acc, DPT, SPT>(a, acc, dtile, b, t0, wd, lb);
+    if (!*gave_up) store_lane_strided<Acc, DPT, SPT>(a, acc, dtile, b, t0, wd, lb);
 }
 
 // Dispatches a tile to the kind's body.

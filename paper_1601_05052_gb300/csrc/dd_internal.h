@@ -20,6 +20,29 @@ inline int elt_bytes(dd_dtype t) { return t == DD_F32 ? 4 : (t == DD_U8 ? 1 : 2)
 // Elements per 16 bytes: the TMA bulk-copy granule.
 inline int align_elems(dd_dtype t) { return 16 / elt_bytes(t); }
 
+// The streams on which an object's kernels (a plan's, or a batch's) were
+// launched, each with an event recorded after its latest launch there.
+// Replacing the tables those launches read waits on these events only (the
+// host blocks for this object's own work, no device-wide synchronisation).
+// Launches made while a stream is being captured into a CUDA graph are not
+// tracked; they only mark the object as captured, after which replaced
+// tables are kept until the object is destroyed, since a graph may still
+// replay launches that read them.
+struct LaunchTracker {
+    static constexpr int kMax = 8;
+    cudaStream_t stream[kMax] = {};
+    cudaEvent_t event[kMax] = {};
+    unsigned long long used[kMax] = {};  // last note() of each slot
+    unsigned long long clock = 0;
+    int n = 0;
+    bool overflow = false;  // an event call failed: wait() synchronises the device
+    bool captured = false;
+    std::mutex mu;
+    void note(cudaStream_t s);  // call after a successful launch on s
+    cudaError_t wait();
+    void destroy();
+};
+
 // Per-variant staging tables of the forward kernel.
 //
 // The DM axis is cut into tiles of Dt trials, the time axis into tiles of Ts
@@ -59,6 +82,9 @@ struct FwdTables {
     int p_elems = 0;
     // largest delay of each DM tile (over its trials and all channels)
     std::vector<int32_t> dtile_max_shift;
+    // stream the device tables were allocated on (stream-ordered; they are
+    // freed on it too)
+    cudaStream_t aux = nullptr;
     // plans with a declared nonzero input column range only:
     // [n_dtiles][n_ttiles] {first, end} chunks whose staged windows reach it
     // (the hull of those chunks; the others add zeros and are skipped)
@@ -105,6 +131,11 @@ struct dd_plan_s {
     dd::AdjState adj;
     int32_t *d_shifts = nullptr;  // device copy of `shifts`
     int *d_err = nullptr;         // device error word (dd::kErr* bits)
+    // plan-owned stream for table uploads and stream-ordered frees
+    cudaStream_t aux = nullptr;
+    dd::LaunchTracker launches;
+    // tables replaced after a launch of this plan was captured into a graph
+    std::vector<dd::FwdTables> retired;
 
     // device mirrors for dd_execute_host, allocated on first use
     void *h_in_dev = nullptr, *h_w_dev = nullptr, *h_out_dev = nullptr;
@@ -133,6 +164,8 @@ bool fwd_variant_compiled(int kind, int dpt, int spt);
 // not fit this plan/device.
 dd_status build_fwd_tables(dd_plan_s *p, const dd_variant &v, FwdTables *out);
 void free_fwd_tables(FwdTables *t);
+// Replaces *cur by next once no tracked launch can still read *cur.
+dd_status replace_fwd_tables(dd_plan_s *p, FwdTables *cur, const FwdTables &next);
 dd_status check_variant_shape(const dd_variant &v);
 
 // Enqueue the forward kernel with the plan's current tables, over time tiles

@@ -24,6 +24,7 @@
 #include <mutex>
 
 #include "dd_internal.h"
+#include "dd_reduce.cuh"
 
 namespace dd {
 namespace {
@@ -109,13 +110,11 @@ __global__ void __launch_bounds__(256, 1) dd_gw_noalloc_kernel(const NoAllocArgs
     }
 }
 
-// gw[c] = sum of the G partial rows, in row order, in FP64.
+// gw[c] = sum of the G partial rows in FP32, in a fixed order.
 __global__ void dd_gw_noalloc_reduce_kernel(const float *part, int G, int C, float *gw) {
     const int c = blockIdx.x * blockDim.x + threadIdx.x;
     if (c >= C) return;
-    double s = 0.0;
-    for (int r = 0; r < G; ++r) s += double(part[(long long)r * C + c]);
-    gw[c] = float(s);
+    gw[c] = fixed_order_sum(part + c, G, C);
 }
 
 // Device address of the scratch array, looked up once per device (with that

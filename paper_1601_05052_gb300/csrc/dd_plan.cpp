@@ -40,6 +40,73 @@ dd_status ok() { return DD_OK; }
 
 bool aligned16(const void *p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
 
+void LaunchTracker::note(cudaStream_t s) {
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(s, &cs) != cudaSuccess) {
+        cudaGetLastError();
+        cs = cudaStreamCaptureStatusActive;  // unknown: treat as captured (keeps tables)
+    }
+    std::lock_guard<std::mutex> lk(mu);
+    if (cs != cudaStreamCaptureStatusNone) {
+        captured = true;
+        return;
+    }
+    ++clock;
+    int i = 0;
+    while (i < n && stream[i] != s) ++i;
+    if (i == n && n == kMax) {
+        // every slot is taken: the least recently used stream's last launch
+        // is waited for here, after which that slot can forget it
+        i = 0;
+        for (int j = 1; j < n; ++j)
+            if (used[j] < used[i]) i = j;
+        if (cudaEventSynchronize(event[i]) != cudaSuccess) {
+            cudaGetLastError();
+            overflow = true;
+        }
+        stream[i] = s;
+    } else if (i == n) {
+        if (cudaEventCreateWithFlags(&event[n], cudaEventDisableTiming) != cudaSuccess) {
+            cudaGetLastError();
+            overflow = true;
+            return;
+        }
+        stream[n++] = s;
+    }
+    used[i] = clock;
+    if (cudaEventRecord(event[i], s) != cudaSuccess) {
+        cudaGetLastError();
+        overflow = true;
+    }
+}
+
+cudaError_t LaunchTracker::wait() {
+    std::lock_guard<std::mutex> lk(mu);
+    for (int i = 0; i < n; ++i) {
+        cudaError_t e = cudaEventSynchronize(event[i]);
+        if (e != cudaSuccess) return e;
+    }
+    if (overflow) return cudaDeviceSynchronize();
+    return cudaSuccess;
+}
+
+void LaunchTracker::destroy() {
+    std::lock_guard<std::mutex> lk(mu);
+    for (int i = 0; i < n; ++i) cudaEventDestroy(event[i]);
+    n = 0;
+}
+
+dd_status replace_fwd_tables(dd_plan_s *p, FwdTables *cur, const FwdTables &next) {
+    cudaError_t e = p->launches.wait();  // no launch of this plan still reads *cur
+    if (p->launches.captured)
+        p->retired.push_back(*cur);  // a captured graph may replay launches that read it
+    else
+        free_fwd_tables(cur);
+    *cur = next;
+    if (e != cudaSuccess) return cuda_fail(e, "waiting for the plan's launches");
+    return DD_OK;
+}
+
 dd_status check_variant_shape(const dd_variant &v) {
     if (!fwd_variant_compiled(v.kind, v.dm_per_thread, v.samples_per_thread))
         return fail(DD_ERR_ARG, "variant (kind, dm_per_thread, samples_per_thread) not compiled");
@@ -287,41 +354,40 @@ dd_status build_fwd_tables(dd_plan_s *p, const dd_variant &v, FwdTables *out) {
             }
     }
 
-    cudaError_t e = cudaMalloc(&t.d_desc, desc.size() * sizeof(int4));
-    if (e != cudaSuccess) return cuda_fail(e, "cudaMalloc(desc)");
-    if (!live.empty()) {
-        e = cudaMalloc(&t.d_live, live.size() * sizeof(int2));
-        if (e == cudaSuccess)
-            e = cudaMemcpy(t.d_live, live.data(), live.size() * sizeof(int2),
-                           cudaMemcpyHostToDevice);
-        if (e != cudaSuccess) {
-            free_fwd_tables(&t);
-            return cuda_fail(e, "live chunk table");
-        }
-    }
-    e = cudaMalloc(&t.d_offs, offs.size() * sizeof(uint16_t));
-    if (e == cudaSuccess && sb) e = cudaMalloc(&t.d_bdesc, bdesc.size() * sizeof(int4));
+    // Stream-ordered allocation and upload on the plan's own stream, which
+    // is then synchronised (only it): the tables are complete before any
+    // launch on another stream can read them, and freeing them later needs
+    // no device-wide synchronisation.
+    t.aux = p->aux;
+    auto upload = [&](void **dst, const void *src, size_t bytes) {
+        cudaError_t r = cudaMallocAsync(dst, bytes, t.aux);
+        if (r == cudaSuccess) r = cudaMemcpyAsync(*dst, src, bytes, cudaMemcpyHostToDevice, t.aux);
+        return r;
+    };
+    cudaError_t e = upload(reinterpret_cast<void **>(&t.d_desc), desc.data(),
+                           desc.size() * sizeof(int4));
+    if (e == cudaSuccess && !live.empty())
+        e = upload(reinterpret_cast<void **>(&t.d_live), live.data(), live.size() * sizeof(int2));
     if (e == cudaSuccess)
-        e = cudaMemcpy(t.d_desc, desc.data(), desc.size() * sizeof(int4), cudaMemcpyHostToDevice);
-    if (e == cudaSuccess)
-        e = cudaMemcpy(t.d_offs, offs.data(), offs.size() * sizeof(uint16_t),
-                       cudaMemcpyHostToDevice);
+        e = upload(reinterpret_cast<void **>(&t.d_offs), offs.data(), offs.size() * sizeof(uint16_t));
     if (e == cudaSuccess && sb)
-        e = cudaMemcpy(t.d_bdesc, bdesc.data(), bdesc.size() * sizeof(int4),
-                       cudaMemcpyHostToDevice);
+        e = upload(reinterpret_cast<void **>(&t.d_bdesc), bdesc.data(), bdesc.size() * sizeof(int4));
+    if (e == cudaSuccess) e = cudaStreamSynchronize(t.aux);
     if (e != cudaSuccess) {
         free_fwd_tables(&t);
-        return cuda_fail(e, "cudaMemcpy(tables)");
+        return cuda_fail(e, "uploading the staging tables");
     }
     *out = t;
     return DD_OK;
 }
 
+// Stream-ordered free on the stream the tables were allocated on; callers
+// make sure no launch still reads them (LaunchTracker::wait, or their own
+// synchronisation).
 void free_fwd_tables(FwdTables *t) {
-    if (t->d_desc) cudaFree(t->d_desc);
-    if (t->d_offs) cudaFree(t->d_offs);
-    if (t->d_bdesc) cudaFree(t->d_bdesc);
-    if (t->d_live) cudaFree(t->d_live);
+    void *ptrs[] = {t->d_desc, t->d_offs, t->d_bdesc, t->d_live};
+    for (void *q : ptrs)
+        if (q) cudaFreeAsync(q, t->aux);
     t->d_desc = nullptr;
     t->d_offs = nullptr;
     t->d_bdesc = nullptr;
@@ -414,6 +480,8 @@ dd_status finish_plan(dd_plan_s *p, dd_plan *out) {
     e = cudaDeviceGetAttribute(&v, cudaDevAttrMaxSharedMemoryPerBlockOptin, p->device);
     if (e != cudaSuccess) return cuda_fail(e, "cudaDeviceGetAttribute(smem)");
     p->smem_optin = size_t(v);
+    e = cudaStreamCreateWithFlags(&p->aux, cudaStreamNonBlocking);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaStreamCreate(plan)");
     e = cudaMalloc(&p->d_shifts, p->shifts.size() * sizeof(int32_t));
     if (e != cudaSuccess) return cuda_fail(e, "cudaMalloc(shifts)");
     e = cudaMemcpy(p->d_shifts, p->shifts.data(), p->shifts.size() * sizeof(int32_t),
@@ -529,7 +597,10 @@ dd_status dd_plan_create_from_shifts(dd_plan *out, int32_t n_chan, int32_t n_dm,
 
 void dd_plan_destroy(dd_plan p) {
     if (!p) return;
+    p->launches.wait();
     free_fwd_tables(&p->fwd);
+    for (FwdTables &t : p->retired) free_fwd_tables(&t);
+    if (p->aux) cudaStreamSynchronize(p->aux);
     free_adj_state(&p->adj);
     if (p->d_err) cudaFree(p->d_err);
     if (p->d_shifts) cudaFree(p->d_shifts);
@@ -540,6 +611,8 @@ void dd_plan_destroy(dd_plan p) {
     if (p->h_in_dev) cudaFree(p->h_in_dev);
     if (p->h_w_dev) cudaFree(p->h_w_dev);
     if (p->h_out_dev) cudaFree(p->h_out_dev);
+    p->launches.destroy();
+    if (p->aux) cudaStreamDestroy(p->aux);
     delete p;
 }
 
@@ -565,11 +638,7 @@ dd_status dd_plan_set_variant(dd_plan p, const dd_variant *v) {
     FwdTables t;
     dd_status s = build_fwd_tables(p, *v, &t);
     if (s != DD_OK) return s;
-    cudaError_t e = cudaDeviceSynchronize();  // no launch may still read the old tables
-    free_fwd_tables(&p->fwd);
-    p->fwd = t;
-    if (e != cudaSuccess) return cuda_fail(e, "cudaDeviceSynchronize");
-    return DD_OK;
+    return replace_fwd_tables(p, &p->fwd, t);  // waits for this plan's launches only
 }
 
 // The variant grid: every compiled (kind, dm_per_thread, samples_per_thread)

@@ -155,8 +155,8 @@ extern "C" dd_status dd_tune(dd_plan p, int32_t budget_ms, dd_tune_report *rep) 
     FwdTables t;
     s = build_fwd_tables(p, best, &t);
     if (s != DD_OK) return s;
-    free_fwd_tables(&p->fwd);
-    p->fwd = t;
+    s = replace_fwd_tables(p, &p->fwd, t);
+    if (s != DD_OK) return s;
     cache_store(plan_signature(p), best);
     return DD_OK;
 }

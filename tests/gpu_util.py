@@ -76,3 +76,17 @@ def random_case(rng, B, C, D, S, max_shift, dtype, monotone=True, weights="unifo
     if dtype == "u8":
         w = synth.quantize_weights_q8(w)
     return sh, x, w
+
+
+def points_by_beam(x, w, sh, pb, pd, pt, dtype):
+    """The oracle at sampled points, one beam at a time (a float beam decodes
+    to FP64 on its own, so large batches never decode whole)."""
+    if dtype == "u8":
+        return oracle.forward_points_u8(x, w, sh, pb, pd, pt), None
+    ref = np.empty(pb.size)
+    ab = np.empty(pb.size)
+    for b in np.unique(pb):
+        m = pb == b
+        ref[m], ab[m] = oracle.forward_points(x[b:b + 1], w, sh, np.zeros(m.sum(), np.int64),
+                                              pd[m], pt[m], dtype=dtype)
+    return ref, ab

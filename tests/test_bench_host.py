@@ -4,6 +4,7 @@ kernel sources and variant it was taken from, and the tuning-experiment table
 is rendered from the run's own results."""
 import json
 import os
+import re
 import sys
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
@@ -21,11 +22,20 @@ def _profile_variant():
 
 
 def test_recorded_traffic_matches_sources_and_variant():
+    """The committed summary's figures are used only with the kernel sources
+    and the variant they were taken from."""
     v = _profile_variant()
-    t = bench.recorded_traffic(v)
+    text = open(os.path.join(ROOT, bench.TRAFFIC_PROFILE)).read()
+    m = re.search(r"kernel source hash: ([0-9a-f]{16})", text)
+    assert m
+    current = text.replace(m.group(0), "kernel source hash: " + bench.kernel_hash())
+    t = bench.recorded_traffic(v, current)
     assert t is not None and 1e8 < t < 3e8  # read + write bytes of one survey launch
-    other = dict(v, stages=v["stages"] + 1)
-    assert bench.recorded_traffic(other) is None
+    assert bench.recorded_traffic(dict(v, stages=v["stages"] + 1), current) is None
+    stale = text.replace(m.group(0), "kernel source hash: 0123456789abcdef")
+    assert bench.recorded_traffic(v, stale) is None
+    # the committed file gives figures exactly when its hash is the sources' own
+    assert (bench.recorded_traffic(v) is not None) == (m.group(1) == bench.kernel_hash())
 
 
 def test_kernel_hash_is_stable_and_covers_the_sources():

@@ -8,7 +8,7 @@ import torch
 import oracle
 import synth
 from paper_1601_05052_gb300 import Batch, Plan
-from gpu_util import assert_float_parity, random_case, to_dev, weights_dev
+from gpu_util import assert_float_parity, points_by_beam, random_case, to_dev, weights_dev
 
 pytestmark = pytest.mark.gpu
 
@@ -74,6 +74,43 @@ def test_batched_96_plus_32_uneven_beams_u8_sampled():
         if attempt == 0:
             rep = batch.tune(budget_ms=20000)
             assert rep["n_tried"] >= 1
+    for p in plans:
+        p.check_device()
+
+
+def test_batched_96_plus_32_uneven_beams_f16_sampled():
+    """The same 96 + 32 beam batch with 16-bit float input (FP32
+    accumulation) in one persistent launch, as the benchmark times it: its
+    default variant and the tuned one, 3000 sampled outputs per setup within
+    1e-4 * sum|w*in| of the FP64 oracle."""
+    hi, lo = synth.setup("lband64_x96_u8"), synth.setup("lowfreq256_u8")
+    plans, data = [], []
+    for s, seed in ((hi, 43), (lo, 44)):
+        s = s.with_(dtype="f16")
+        sh = oracle.shift_table(s.freqs(), s.f_ref, s.t_samp, s.dms())
+        pulses = synth.pulse_plan(s, seed, amp=(3.0, 6.0))
+        x = synth.make_input(s, sh, seed=seed, pulses=pulses)
+        w = np.ones(s.n_chan, np.float32)
+        plans.append(Plan.from_setup(s))
+        data.append((s, sh, x, w))
+    batch = Batch(plans)
+    xs = [to_dev(d[2], "f16") for d in data]
+    ws = [weights_dev(d[3], "f16") for d in data]
+    rng = np.random.default_rng(6)
+    for attempt in range(2):
+        outs = batch.execute(xs, ws)
+        torch.cuda.synchronize()
+        for (s, sh, x, w), o in zip(data, outs):
+            n = 3000
+            pb = rng.integers(0, s.batch, n)
+            pd = rng.integers(0, s.n_dm, n)
+            pt = rng.integers(0, s.n_out, n)
+            ref, ab = points_by_beam(x, w, sh, pb, pd, pt, "f16")
+            got = o[torch.from_numpy(pb).cuda(), torch.from_numpy(pd).cuda(),
+                    torch.from_numpy(pt).cuda()].cpu().numpy()
+            assert_float_parity(got, ref, ab, what="f16 batch %s, attempt %d" % (s.name, attempt))
+        if attempt == 0:
+            batch.tune(budget_ms=15000)
     for p in plans:
         p.check_device()
 
@@ -151,3 +188,33 @@ def test_per_plan_tile_shapes_in_one_launch(dtype):
     assert tried == 4
     for p in plans:
         p.check_device()
+
+
+@pytest.mark.parametrize("kind", [0, 5])
+def test_batch_tiles_with_fewer_chunks_than_stages(kind):
+    """Plans of 16 channels staged 16 at a time have one chunk per tile, fewer
+    than the staging depth, so a CTA's staging warp never waits for the
+    others and can reach the next work item first; every tile of many must
+    still be summed exactly once (8-bit input, exact)."""
+    rng = np.random.default_rng(60 + kind)
+    cases, plans = [], []
+    for B, D, S in ((40, 64, 3000), (24, 32, 1000)):
+        sh = np.sort(rng.integers(0, 200, size=(D, 16)), axis=0)
+        x = rng.integers(0, 256, size=(B, 16, synth.padded_stride(S + int(sh.max()), "u8")),
+                         dtype=np.uint8)
+        w = rng.integers(-300, 300, size=16).astype(np.int32)
+        cases.append((sh, x, w, S))
+        plans.append(Plan(shifts=sh, n_out=S, batch=B, dtype="u8"))
+    batch = Batch(plans)
+    batch.variant = dict(kind=kind, dm_per_thread=4, samples_per_thread=8, warps_dm=4,
+                         warps_time=2, chans_per_stage=16, stages=3)
+    xs = [to_dev(c[1], "u8") for c in cases]
+    ws = [weights_dev(c[2], "u8") for c in cases]
+    for _ in range(3):
+        outs = batch.execute(xs, ws)
+        for (sh, x, w, S), o in zip(cases, outs):
+            np.testing.assert_array_equal(o.cpu().numpy().astype(np.int64),
+                                          oracle.forward_u8(x, w, sh, S))
+    for p in plans:
+        p.check_device()
+

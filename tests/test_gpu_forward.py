@@ -10,7 +10,8 @@ import torch
 import oracle
 import synth
 from paper_1601_05052_gb300 import Plan, variants
-from gpu_util import assert_float_parity, check_full, random_case, to_dev, weights_dev
+from gpu_util import (assert_float_parity, check_full, points_by_beam, random_case, to_dev,
+                      weights_dev)
 
 pytestmark = pytest.mark.gpu
 DTYPES = ["f32", "f16", "bf16", "u8"]
@@ -333,6 +334,41 @@ def test_survey_scale_f32_sampled():
     plan.check_device()
 
 
+@pytest.mark.parametrize("dtype", ["u8", "f16", "bf16"])
+def test_survey_scale_narrow_inputs_sampled(dtype):
+    """The survey workload (1024 ch, 2048 trials, 20000 samples) with 8-bit
+    and 16-bit input in the plan's default variant (the wide sub-band kind
+    the benchmark times for these types), weights U(0.5, 1.5) with 5 %
+    masked (Q8 integers for 8-bit input): 4000 sampled outputs, the ten
+    pulses and the corners, bit-exact for u8, within 1e-4 * sum|w*in| for
+    f16 / bf16."""
+    s = synth.setup("apertif_survey").with_(dtype=dtype)
+    sh = oracle.shift_table(s.freqs(), s.f_ref, s.t_samp, s.dms())
+    pulses = synth.pulse_plan(s, 2, n_per_beam=10)
+    x = synth.make_input(s, sh, seed=2, pulses=pulses)
+    w = synth.make_weights(s.n_chan, 2, "uniform")
+    if dtype == "u8":
+        w = synth.quantize_weights_q8(w)
+    plan = Plan.from_setup(s)
+    assert plan.variant["kind"] == 4, plan.variant
+    out = plan.execute(to_dev(x, dtype), weights_dev(w, dtype))
+    torch.cuda.synchronize()
+    rng = np.random.default_rng(23)
+    n = 4000
+    pd = np.concatenate([rng.integers(0, s.n_dm, n), [p[1] for p in pulses],
+                         [0, s.n_dm - 1, s.n_dm - 1, 0]])
+    pt = np.concatenate([rng.integers(0, s.n_out, n), [p[2] for p in pulses],
+                         [0, s.n_out - 1, 0, s.n_out - 1]])
+    pb = np.zeros_like(pd)
+    got = out[0][torch.from_numpy(pd).cuda(), torch.from_numpy(pt).cuda()].cpu().numpy()
+    ref, ab = points_by_beam(x, w, sh, pb, pd, pt, dtype)
+    if dtype == "u8":
+        np.testing.assert_array_equal(got.astype(np.int64), ref)
+    else:
+        assert_float_parity(got, ref, ab, what="apertif_survey %s sampled" % dtype)
+    plan.check_device()
+
+
 def test_bounded_wait_reports_timeout_and_context_survives():
     """A kernel waiting on a barrier nothing completes gives up after its
     budget, the host reads DD_ERR_TIMEOUT, and the next launch still works."""
@@ -383,3 +419,69 @@ def test_stream_equals_one_long_dedispersion(dtype):
     st.reset()
     again = st.push(to_dev(np.ascontiguousarray(x[:, :, :S]), dtype), wd).cpu().numpy()
     np.testing.assert_array_equal(again, outs[0])
+
+
+def test_binding_rejects_buffers_the_kernels_cannot_take():
+    """A caller's buffer pointer goes to a kernel as is: host tensors, other
+    shapes or types, and non-contiguous views are refused before any launch."""
+    from paper_1601_05052_gb300 import Batch
+    rng = np.random.default_rng(41)
+    sh, x, w = random_case(rng, 2, 9, 7, 100, 30, "f32")
+    plan = Plan(shifts=sh, n_out=100, batch=2)
+    xd, wd = to_dev(np.nan_to_num(x), "f32"), weights_dev(w, "f32")
+    bad_outs = [torch.empty(plan.out_shape),  # host memory
+                torch.empty((2, 7, 99), device="cuda"),  # shape
+                torch.empty(plan.out_shape, dtype=torch.float16, device="cuda"),  # type
+                torch.empty((2, 7, 200), device="cuda")[:, :, ::2]]  # non-contiguous
+    for o in bad_outs:
+        with pytest.raises(ValueError):
+            plan.execute(xd, wd, out=o)
+    with pytest.raises(ValueError):
+        plan.execute(xd.cpu(), wd)
+    g = torch.zeros(plan.out_shape, device="cuda")
+    with pytest.raises(ValueError):
+        plan.adjoint(g, wd, xd.half())  # grad_w needs the FP32 input
+    with pytest.raises(ValueError):
+        plan.adjoint(g, None, xd)  # grad_in needs the weights
+    batch = Batch([plan])
+    with pytest.raises(ValueError):
+        batch.execute([xd, xd], [wd])
+    with pytest.raises(ValueError):
+        batch.execute([xd], [wd], [bad_outs[3]])
+    ok = plan.execute(xd, wd, out=torch.empty(plan.out_shape, device="cuda"))
+    ref, ab = oracle.forward(np.nan_to_num(x), w, sh, 100, with_absum=True)
+    assert_float_parity(ok.cpu().numpy(), ref, ab, what="after refusals")
+
+
+def test_set_variant_waits_for_this_plans_launches_only():
+    """dd_plan_set_variant replaces the tables that launches read. It waits
+    for the plan's own launches (on every stream they went to, more streams
+    than it keeps slots for) instead of the whole device; each launch made
+    before the change still reads the old, intact tables."""
+    from paper_1601_05052_gb300 import compute_shifts
+    C, D, S = 256, 512, 6000
+    freqs = 1420.0 + np.arange(C) * (300.0 / C)
+    sh = compute_shifts(freqs, freqs[-1], 50e-6, np.arange(D) * 0.25).astype(np.int64)
+    rng = np.random.default_rng(42)
+    plan = Plan(shifts=sh, n_out=S, batch=1)
+    x = rng.standard_normal(plan.in_shape).astype(np.float32)
+    w = rng.uniform(0.5, 1.5, C).astype(np.float32)
+    xd, wd = to_dev(x, "f32"), weights_dev(w, "f32")
+    kinds = [v for v in variants() if v["kind"] in (0, 4) and v["stages"] == 2
+             and v["chans_per_stage"] == 16 and _fits(sh, S, v)][:3]
+    assert len(kinds) >= 2
+    streams = [torch.cuda.Stream() for _ in range(10)]
+    outs = []
+    for k, v in enumerate(kinds):
+        plan.variant = v
+        for st in streams:  # launches on 10 streams, then the next change at once
+            o = torch.empty(plan.out_shape, device="cuda")
+            with torch.cuda.stream(st):
+                plan.execute(xd, wd, out=o, stream=st)
+            outs.append(o)
+    torch.cuda.synchronize()
+    ref, ab = oracle.forward(x, w, sh, S, with_absum=True)
+    for o in outs:
+        assert_float_parity(o.cpu().numpy(), ref, ab, what="launch before a variant change")
+    plan.check_device()
+

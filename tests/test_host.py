@@ -104,3 +104,23 @@ def test_variant_grid():
         assert v["chans_per_stage"] in (4, 8, 16) and 2 <= v["stages"] <= 4
     # kind 4 covers DM tiles of 128 trials
     assert any(v["kind"] == 4 and v["dm_per_thread"] * v["warps_dm"] == 128 for v in vs)
+
+
+def test_plan_statistics_on_a_hand_table():
+    """The plan statistics tool counts relative delay patterns per (DM tile,
+    channel group) and equal adjacent delays on a table worked by hand."""
+    from paper_1601_05052_gb300 import plan_stats
+    sh = np.array([[0, 0, 0, 0],
+                   [3, 2, 1, 0],
+                   [6, 4, 2, 0],
+                   [4, 3, 2, 1]])  # row 3 = row 1's pattern, base delay 1
+    count, span = plan_stats.delay_patterns(sh, dt=4, group=4)
+    assert count.tolist() == [[3]] and span.tolist() == [[1]]
+    count, span = plan_stats.delay_patterns(sh, dt=2, group=2)
+    # tile 0: groups (c0,c1): rel (0,0),(1,0) -> 2; (c2,c3): (0,0),(1,0) -> 2
+    # tile 1: (c0,c1): (2,0),(1,0) -> 2; (c2,c3): (2,0),(1,0) -> 2
+    assert count.tolist() == [[2, 2], [2, 2]]
+    assert plan_stats.shared_adjacent_delays(np.array([[0, 1], [0, 2]])) == 0.5
+    lane, sub, ratio = plan_stats.shared_words(sh, dt=4, ts=8, group=4)
+    assert lane == 4 * 8 * 4
+    assert sub == 4 * 8 * 1 + (1 + 3 * 8) * 5 and ratio == lane / sub
