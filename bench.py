@@ -65,7 +65,7 @@ def _args():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--only", choices=["uneven_u8", "uneven_f16", "uneven_f32", "f32_96beams",
                                        "f32_hbm_bound", "survey_precisions", "differentiable",
-                                       "small_graph"],
+                                       "small_graph", "lofar"],
                     help="run one secondary workload alone (for profiling its kernels)")
     ap.add_argument("--no-tune", action="store_true",
                     help="with --only: keep the plans' starting variants (the built-in default, "
@@ -321,7 +321,7 @@ def _case_uneven(torch, flush, n_rep, dtypes=("u8", "f16", "f32"), tune=True, va
     return out
 
 
-def _case_small_graph(torch, n_rep, per_graph=200):
+def _case_small_graph(torch, n_rep, per_graph=200, tune=True):
     """The 64-channel, 64-trial, 4096-sample workload in FP32 (unit weights)
     and its 8-bit / FP16 / BF16 forms (weights U(0.5, 1.5), 5 % masked, Q8
     integers for 8-bit input): a microsecond-scale launch, so `per_graph`
@@ -344,6 +344,8 @@ def _case_small_graph(torch, n_rep, per_graph=200):
         if dtype == "u8":
             w = synth.quantize_weights_q8(w)
         p = Plan.from_setup(s)
+        if tune:
+            p.tune(budget_ms=3000)
         xt = torch.from_numpy(x)
         if dtype == "bf16":
             xt = xt.view(torch.bfloat16)
@@ -458,6 +460,38 @@ def _case_survey_precisions(torch, flush, n_rep, f32_ms=None):
     return out
 
 
+def _case_lofar(torch, n_rep, peaks, tune=True, variant=None):
+    """The paper's LOFAR instance (Section IV): 32 channels of 0.195 MHz from
+    138 MHz, 5 us sampling, 2048 trial DMs 0-511.75, 200000 samples (1 s),
+    FP32, unit weights. One DM step moves the lowest channel by ~900
+    samples, so a trial's input window is shared with almost no other trial
+    (the paper's low-reuse regime). The 260 MB input is larger than L2: no
+    flush."""
+    import synth
+    from paper_1601_05052_gb300 import Plan
+    g = torch.Generator(device="cuda")
+    s = synth.setup("lofar")
+    p = Plan.from_setup(s)
+    if variant:
+        p.variant = variant
+    elif tune:
+        p.tune(budget_ms=8000)
+    x = _rand_input(torch, g, p, 13, "f32")
+    w = torch.ones(p.n_chan, device="cuda")
+    o = torch.empty(p.out_shape, device="cuda")
+    t = statistics.median(_time_steps(lambda: p.execute(x, w, o), n_rep, 2, None, torch))
+    adds = s.batch * s.n_dm * s.n_out * s.n_chan
+    n_sm = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
+    alu_peak = n_sm * 128 * peaks.get("sm_max_mhz", 2070.0) * 1e6
+    comp = (x.numel() * 4 + o.numel() * 4) / (t * 1e-3)
+    return {"workload": "LOFAR: 32 ch (138-144.25 MHz, 5 us) x 2048 DM (0-511.75) x 200000 "
+                        "samples, FP32", "unit": UNIT,
+            "value": s.batch * s.n_dm * s.n_out / (t * 1e-3), "ms": t, "variant": p.variant,
+            "gflops": adds / (t * 1e-3) / 1e9, "alu_frac": adds / (t * 1e-3) / alu_peak,
+            "effective_hbm_gbs": comp / 1e9, "hbm_frac": comp / 1e9 / peaks["hbm_gbs"],
+            "l2": "input larger than L2, no flush"}
+
+
 # The HBM-bound point runs this variant (the tuner's usual pick there), so
 # that its DRAM counters in profiles/fwd_hbm_bound_4dm_f32.md belong to the
 # kernel it times.
@@ -471,6 +505,7 @@ def _extras(torch, flush, peaks, steps, f32_ms=None):
     return {"uneven_beams": _case_uneven(torch, flush, n_rep),
             "survey_precisions": _case_survey_precisions(torch, flush, n_rep, f32_ms),
             "small_graph_64ch": _case_small_graph(torch, n_rep),
+            "lofar_f32": _case_lofar(torch, n_rep, peaks),
             "f32_96beams_64ch": _case_96beams(torch, flush, n_rep, peaks),
             "f32_hbm_bound_4dm_384beams": _case_96beams(torch, flush, n_rep, peaks,
                                                         variant=HBM_BOUND_VARIANT,
@@ -498,7 +533,9 @@ def run_only(args):
                             variant=variant or HBM_BOUND_VARIANT,
                             name="lband64_4dm_x384")
     elif args.only == "small_graph":
-        out = _case_small_graph(torch, n)
+        out = _case_small_graph(torch, n, tune=tune)
+    elif args.only == "lofar":
+        out = _case_lofar(torch, n, peaks, tune=tune, variant=variant)
     elif args.only == "survey_precisions":
         out = _case_survey_precisions(torch, flush, n)
     else:

@@ -236,7 +236,8 @@ dd_status configure(dd_batch_s *bt, const std::vector<dd_variant> &pv) {
         a.n_dtiles = t.n_dtiles;
         a.n_ttiles = t.n_ttiles;
         a.B = p->B;
-        a.desc = t.d_desc;
+        a.copies = t.d_copies;
+        a.n_copies = t.n_copies;
         a.offs = t.d_offs;
         a.bdesc = t.d_bdesc;
         a.n_blocks = t.n_blocks;

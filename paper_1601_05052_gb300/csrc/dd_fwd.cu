@@ -163,7 +163,8 @@ dd_status launch_forward(dd_plan_s *p, const FwdTables &t, const void *in, const
     a.n_dtiles = t.n_dtiles;
     a.n_ttiles = t.n_ttiles;
     a.B = p->B;
-    a.desc = t.d_desc;
+    a.copies = t.d_copies;
+    a.n_copies = t.n_copies;
     a.offs = t.d_offs;
     a.bdesc = t.d_bdesc;
     a.n_blocks = t.n_blocks;

@@ -109,7 +109,8 @@ struct FwdArgs {
     int n_dtiles, n_ttiles, B;
     int ttile0;  // one-shot launches: time tile of grid row 0 (a launch may cover a range)
     int dtile0;  // one-shot launches: DM tile of grid column 0
-    const int4 *desc;
+    const int4 *copies;  // staging copies [n_dtiles][n_chunks][n_copies]
+    int n_copies;
     const uint16_t *offs;
     const int4 *bdesc;  // sub-band kinds: build blocks [n_dtiles][n_chunks][n_blocks]
     int n_blocks;       // sub-band kinds
@@ -185,7 +186,7 @@ struct Stager {
     const FwdArgs &a;
     const T *in_b;
     long long t0;
-    const int4 *desc_k;
+    const int4 *copies_k;  // this DM tile's staging copies
     const void *tab_k;    // kind 0/1: trial offsets; sub-band kinds: group offsets
     const int4 *bdesc_k;  // sub-band kinds: this DM tile's build blocks
     uint32_t tab_bytes;   // per chunk, both tables
@@ -195,24 +196,37 @@ struct Stager {
     bool subband;
     int kc0;  // chunk k of the tile's loop is chunk kc0 + k of the plan
 
-    // Descriptor of this lane's channel in chunk k (zero beyond the chunk).
+    // This lane's first staging copy of chunk k (copy `lane`; zero if none).
     __device__ __forceinline__ int4 desc(int k, int lane) const {
-        const int c = (kc0 + k) * a.cch + lane;
-        return (lane < a.cch && c < a.C) ? desc_k[c] : make_int4(0, 0, 0, 0);
+        return lane < a.n_copies ? copies_k[(size_t)(kc0 + k) * a.n_copies + lane]
+                                 : make_int4(0, 0, 0, 0);
     }
 
-    // Warp-cooperative: stage chunk k into `slot`, each lane < channels
-    // copying its channel's window (descriptor `dsc` preloaded), lane 0 the
+    // Bytes copy d moves (a window may reach past the row's padded end only
+    // in the last time tile; it is cut there, on a 16-byte boundary).
+    __device__ __forceinline__ uint32_t copy_bytes(int4 d) const {
+        return d.y ? uint32_t(min((long long)d.y, a.stride - (t0 + d.x))) * uint32_t(sizeof(T))
+                   : 0u;
+    }
+
+    __device__ __forceinline__ void copy(unsigned char *sb, int c0, int4 d, uint64_t *full) const {
+        const uint32_t bytes = copy_bytes(d);
+        if (bytes)
+            bulk_g2s(sb + (size_t)d.z * sizeof(T),
+                     in_b + (long long)(c0 + d.w) * a.stride + t0 + d.x, bytes, full);
+    }
+
+    // Warp-cooperative: stage chunk k into `slot`. Lane l issues the chunk's
+    // copies l, l + 32, ... (its first, `dsc`, preloaded), lane 0 also the
     // tables and weights. All 32 lanes of one warp must call it.
     __device__ __forceinline__ void issue(int k, int slot, int4 dsc, uint64_t *full,
                                           int lane) const {
         unsigned char *sb = stage0 + slot * stage_bytes;
         const int c0 = (kc0 + k) * a.cch;
         const int nch = min(a.cch, a.C - c0);
-        const long long g0 = t0 + dsc.x;
-        uint32_t bytes = 0;
-        if (lane < nch)
-            bytes = uint32_t(min((long long)dsc.y, a.stride - g0)) * uint32_t(sizeof(T));
+        const int4 *more = copies_k + (size_t)(kc0 + k) * a.n_copies;
+        uint32_t bytes = copy_bytes(dsc);
+        for (int m = lane + 32; m < a.n_copies; m += 32) bytes += copy_bytes(more[m]);
         uint32_t total = bytes;
 #pragma unroll
         for (int m = 16; m >= 1; m >>= 1) total += __shfl_xor_sync(0xffffffffu, total, m);
@@ -220,9 +234,8 @@ struct Stager {
         if (lane == 0) mbar_arrive_expect_tx(full, total + tab_bytes + w_bytes);
         __syncwarp();
         fence_proxy_async_smem();
-        if (bytes)
-            bulk_g2s(sb + (size_t)dsc.z * sizeof(T), in_b + (long long)(c0 + lane) * a.stride + g0,
-                     bytes, full);
+        copy(sb, c0, dsc, full);
+        for (int m = lane + 32; m < a.n_copies; m += 32) copy(sb, c0, more[m], full);
         if (lane == 0) {
             unsigned char *tb = sb + a.stage_data_bytes;
             if (!subband) {
@@ -250,7 +263,7 @@ __device__ __forceinline__ Stager<T> make_stager(const FwdArgs &a, int dtile, in
     Stager<T> s{a,
                 static_cast<const T *>(a.in) + (long long)b * a.C * a.stride,
                 t0,
-                a.desc + (size_t)dtile * a.C_pad,
+                a.copies + (size_t)dtile * ((a.C + a.cch - 1) / a.cch) * a.n_copies,
                 subband ? static_cast<const void *>(a.offs + (size_t)dtile * g_pad * a.Dt)
                         : static_cast<const void *>(a.offs + (size_t)dtile * a.C_pad * a.Dt),
                 subband ? a.bdesc + (size_t)dtile * ((a.C + a.cch - 1) / a.cch) * a.n_blocks

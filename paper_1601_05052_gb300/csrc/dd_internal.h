@@ -46,18 +46,23 @@ struct LaunchTracker {
 // Per-variant staging tables of the forward kernel.
 //
 // The DM axis is cut into tiles of Dt trials, the time axis into tiles of Ts
-// output samples. For DM tile k and channel c, every trial of the tile reads
-// input samples [t0 + smin, t0 + smax + Ts) of row c, where smin/smax are
-// the tile's smallest/largest delay in that channel (Section III-B: a 2-D
-// work-group shares the union of its trials' inputs). That window, widened
-// to 16-byte granules, is copied into shared memory once per stage.
+// output samples. For DM tile k and channel c, trial d of the tile reads
+// input samples [t0 + shift, t0 + shift + Ts) of row c (Section III-B: a 2-D
+// work-group shares the union of its trials' inputs). The trials' windows,
+// in delay order, are merged while they overlap or touch, and each merged
+// window, widened to 16-byte granules, is copied into shared memory once per
+// stage (the sub-band kinds always take the whole union [t0 + smin, t0 + smax
+// + Ts) as one window). Where neighbouring trials' delays differ by more
+// than Ts, a channel thus stages one window per trial rather than a union
+// that is mostly gaps.
 //
-//   desc[k][c] = {win_start (elements, relative to t0, 16-byte aligned),
-//                 win_len (elements, multiple of 16 bytes),
-//                 smem_off (element offset of the window in the stage buffer),
-//                 0}
+//   copies[k][j][m] = {win_start (elements, relative to t0, 16-byte aligned),
+//                      win_len (elements, multiple of 16 bytes; 0 = none),
+//                      smem_off (element offset in the stage buffer),
+//                      channel - first channel of chunk j}
+//                     for the m-th copy of chunk j (capacity n_copies)
 //   offs[k][c][i] = smem element offset of sample t0 of trial k*Dt + i
-//                   in channel c (= smem_off + shift - win_start)
+//                   in channel c (= smem_off + shift - win_start of its window)
 // Input segments of dd_execute_host's copy/compute pipeline.
 constexpr int kHostSegments = 8;
 
@@ -70,7 +75,8 @@ struct FwdTables {
     int stage_data_bytes = 0;    // rounded to 16
     int stage_offs_bytes = 0;    // chans_per_stage * Dt * 2, rounded to 16
     size_t smem_bytes = 0;       // dynamic shared memory of one CTA
-    int4 *d_desc = nullptr;
+    int4 *d_copies = nullptr;    // [n_dtiles][n_chunks][n_copies]
+    int n_copies = 0;
     uint16_t *d_offs = nullptr;
     // sub-band kinds only: d_offs holds per-group trial offsets into the
     // partial-sum buffer, [n_dtiles][C_pad/4][Dt]; d_bdesc the build blocks

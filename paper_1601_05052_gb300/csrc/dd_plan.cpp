@@ -211,6 +211,10 @@ dd_status build_fwd_tables(dd_plan_s *p, const dd_variant &v, FwdTables *out) {
     if (sb && t.Dt % 8 != 0) return fail(DD_ERR_ARG, "sub-band variants need 8 | DM tile");
 
     const int G_pad = t.C_pad / kSbGroup;
+    // desc: each channel's union window {ws, len, soff} per DM tile (the
+    // sub-band build reads it); copies: the staging copies of each (DM tile,
+    // chunk) {ws, len, soff, channel in the chunk}, laid out with a common
+    // capacity once every chunk is known.
     std::vector<int4> desc(size_t(t.n_dtiles) * t.C_pad, make_int4(0, 0, 0, 0));
     std::vector<uint16_t> offs(sb ? size_t(t.n_dtiles) * G_pad * t.Dt
                                   : size_t(t.n_dtiles) * t.C_pad * t.Dt, 0);
@@ -218,33 +222,75 @@ dd_status build_fwd_tables(dd_plan_s *p, const dd_variant &v, FwdTables *out) {
     // capacity once every chunk is known
     const int n_chunks = (p->C + cch - 1) / cch;
     std::vector<std::vector<int4>> blocks(sb ? size_t(t.n_dtiles) * n_chunks : 0);
+    std::vector<std::vector<int4>> copies(size_t(t.n_dtiles) * n_chunks);
     int64_t stage_max = 0, p_max = 0;
     t.dtile_max_shift.assign(size_t(t.n_dtiles), 0);
+    std::vector<int32_t> tsh(size_t(t.Dt));
+    std::vector<int> order(size_t(t.Dt)), seg_of(size_t(t.Dt));
+    std::vector<int64_t> seg_ws, seg_soff;
     for (int k = 0; k < t.n_dtiles; ++k) {
         const int d0 = k * t.Dt, d1 = std::min(p->D, d0 + t.Dt);
+        const int nd = d1 - d0;
         for (int c0 = 0; c0 < p->C; c0 += cch) {
             int64_t soff = 0;
+            std::vector<int4> &cl = copies[size_t(k) * n_chunks + c0 / cch];
             for (int c = c0; c < std::min(p->C, c0 + cch); ++c) {
                 int32_t smin = std::numeric_limits<int32_t>::max(), smax = 0;
-                for (int d = d0; d < d1; ++d) {
-                    const int32_t sh = p->shifts[size_t(d) * p->C + c];
-                    smin = std::min(smin, sh);
-                    smax = std::max(smax, sh);
+                for (int i = 0; i < nd; ++i) {
+                    tsh[size_t(i)] = p->shifts[size_t(d0 + i) * p->C + c];
+                    smin = std::min(smin, tsh[size_t(i)]);
+                    smax = std::max(smax, tsh[size_t(i)]);
                 }
                 t.dtile_max_shift[size_t(k)] = std::max(t.dtile_max_shift[size_t(k)], smax);
-                const int64_t ws = floor_to(smin, al);
-                const int64_t len = round_up(smax + t.Ts - ws, al);
-                if (soff + len > 65536) return fail(DD_ERR_ARG, "stage too large for variant");
-                desc[size_t(k) * t.C_pad + c] = make_int4(int(ws), int(len), int(soff), 0);
+                {
+                    const int64_t ws = floor_to(smin, al);
+                    desc[size_t(k) * t.C_pad + c] =
+                        make_int4(int(ws), int(round_up(smax + t.Ts - ws, al)), int(soff), 0);
+                }
+                // Windows [shift, shift + Ts) of the tile's trials, in delay
+                // order, are merged while they overlap or touch; the
+                // sub-band kinds take the whole union as one window. A
+                // channel whose delay steps by more than a time tile between
+                // trials (low frequencies, coarse DM grids, fine sampling)
+                // thus stages one window per trial instead of a union that
+                // is mostly gaps.
+                for (int i = 0; i < nd; ++i) order[size_t(i)] = i;
+                std::sort(order.begin(), order.begin() + nd,
+                          [&](int x, int y) { return tsh[size_t(x)] < tsh[size_t(y)]; });
+                seg_ws.clear();
+                seg_soff.clear();
+                int64_t lo = tsh[size_t(order[0])], hi = lo;
+                auto close_seg = [&]() -> bool {
+                    const int64_t ws = floor_to(lo, al);
+                    const int64_t len = round_up(hi + t.Ts - ws, al);
+                    if (soff + len > 65536) return false;
+                    cl.push_back(make_int4(int(ws), int(len), int(soff), c - c0));
+                    seg_ws.push_back(ws);
+                    seg_soff.push_back(soff);
+                    soff += len;
+                    return true;
+                };
+                for (int r = 0; r < nd; ++r) {
+                    const int i = order[size_t(r)];
+                    const int64_t sh = tsh[size_t(i)];
+                    if (!sb && sh > hi + t.Ts) {
+                        if (!close_seg()) return fail(DD_ERR_ARG, "stage too large for variant");
+                        lo = sh;
+                    }
+                    hi = std::max<int64_t>(hi, sh);
+                    seg_of[size_t(i)] = int(seg_ws.size());
+                }
+                if (!close_seg()) return fail(DD_ERR_ARG, "stage too large for variant");
                 if (!sb) {
                     for (int i = 0; i < t.Dt; ++i) {
-                        const int d = d0 + i;
-                        const int64_t o =
-                            d < p->D ? soff + p->shifts[size_t(d) * p->C + c] - ws : soff;
+                        int64_t o = seg_soff[0];  // trials beyond D: any in-range offset
+                        if (i < nd) {
+                            const size_t q = size_t(seg_of[size_t(i)]);
+                            o = seg_soff[q] + tsh[size_t(i)] - seg_ws[q];
+                        }
                         offs[(size_t(k) * t.C_pad + c) * t.Dt + i] = static_cast<uint16_t>(o);
                     }
                 }
-                soff += len;
             }
             stage_max = std::max(stage_max, soff);
             if (sb) {
@@ -294,6 +340,12 @@ dd_status build_fwd_tables(dd_plan_s *p, const dd_variant &v, FwdTables *out) {
             }
         }
     }
+    // staging copies with a common capacity (length-0 entries pad)
+    t.n_copies = 1;
+    for (const auto &cl : copies) t.n_copies = std::max<int>(t.n_copies, int(cl.size()));
+    std::vector<int4> copy_tab(copies.size() * size_t(t.n_copies), make_int4(0, 0, 0, 0));
+    for (size_t i = 0; i < copies.size(); ++i)
+        std::copy(copies[i].begin(), copies[i].end(), copy_tab.begin() + i * size_t(t.n_copies));
     std::vector<int4> bdesc;
     if (sb) {
         // Worker w of `parts` builds blocks w, w + parts, ... of a chunk in
@@ -341,10 +393,8 @@ dd_status build_fwd_tables(dd_plan_s *p, const dd_variant &v, FwdTables *out) {
                 int first = -1, last = -1;
                 for (int j = 0; j < n_chunks; ++j) {
                     bool any = false;
-                    for (int c = j * cch; c < std::min(p->C, (j + 1) * cch) && !any; ++c) {
-                        const int4 d = desc[size_t(k) * t.C_pad + c];
-                        any = t0 + d.x < p->nz_hi && t0 + d.x + d.y > p->nz_lo;
-                    }
+                    for (const int4 &d : copies[size_t(k) * n_chunks + j])
+                        any = any || (t0 + d.x < p->nz_hi && t0 + d.x + d.y > p->nz_lo);
                     if (any) {
                         if (first < 0) first = j;
                         last = j;
@@ -364,8 +414,8 @@ dd_status build_fwd_tables(dd_plan_s *p, const dd_variant &v, FwdTables *out) {
         if (r == cudaSuccess) r = cudaMemcpyAsync(*dst, src, bytes, cudaMemcpyHostToDevice, t.aux);
         return r;
     };
-    cudaError_t e = upload(reinterpret_cast<void **>(&t.d_desc), desc.data(),
-                           desc.size() * sizeof(int4));
+    cudaError_t e = upload(reinterpret_cast<void **>(&t.d_copies), copy_tab.data(),
+                           copy_tab.size() * sizeof(int4));
     if (e == cudaSuccess && !live.empty())
         e = upload(reinterpret_cast<void **>(&t.d_live), live.data(), live.size() * sizeof(int2));
     if (e == cudaSuccess)
@@ -385,10 +435,10 @@ dd_status build_fwd_tables(dd_plan_s *p, const dd_variant &v, FwdTables *out) {
 // make sure no launch still reads them (LaunchTracker::wait, or their own
 // synchronisation).
 void free_fwd_tables(FwdTables *t) {
-    void *ptrs[] = {t->d_desc, t->d_offs, t->d_bdesc, t->d_live};
+    void *ptrs[] = {t->d_copies, t->d_offs, t->d_bdesc, t->d_live};
     for (void *q : ptrs)
         if (q) cudaFreeAsync(q, t->aux);
-    t->d_desc = nullptr;
+    t->d_copies = nullptr;
     t->d_offs = nullptr;
     t->d_bdesc = nullptr;
     t->d_live = nullptr;

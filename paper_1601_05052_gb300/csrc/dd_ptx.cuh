@@ -75,15 +75,20 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
 // (and sets kErrWaitTimeout in *err) if the budget ran out.
 //
 // `gave_up` (shared memory, nullable) is the CTA's give-up flag: a wait that
-// finds it set returns false at once, and a wait that runs out sets it. Once
-// one hand-off of a CTA is lost its barriers' phases are out of step (a later
-// parity test could pass on a stale phase), so every later wait of the CTA
-// fails fast and the caller skips the work that depended on it.
+// has to spin and finds it set returns false at once, and a wait that runs
+// out sets it. Once one hand-off of a CTA is lost its barriers' phases are
+// out of step (a later parity test could pass on a stale phase), so later
+// waits of the CTA fail fast, the caller skips the work that depended on
+// them, and no result of the CTA is stored after the flag is set.
 __device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity, int *err,
                                                   unsigned long long budget_ns = kWaitBudgetNs,
                                                   volatile int *gave_up = nullptr) {
-    if (gave_up && *gave_up) return false;
+    // A phase that has already completed is taken without reading the flag
+    // (the common case costs one try_wait); a CTA that gave up learns it at
+    // its next wait that has to spin, and its callers check the flag before
+    // storing results.
     if (mbar_try_wait(bar, parity)) return true;
+    if (gave_up && *gave_up) return false;
     const unsigned long long t0 = globaltimer_ns();
     for (;;) {
         for (int i = 0; i < 64; ++i)
