@@ -73,6 +73,8 @@ def _args():
     ap.add_argument("--variant", default=None,
                     help="with --only uneven_*/f32_96beams: JSON forward variant to use instead "
                          "of tuning (e.g. one a tuned run printed)")
+    ap.add_argument("--n-out", type=int, default=None,
+                    help="with --only lofar: output samples (default: the full 200000)")
     ap.add_argument("--tune-ms", type=int, default=0,
                     help="auto-tune the forward variant for this budget first (0 = no)")
     return ap.parse_args()
@@ -460,7 +462,7 @@ def _case_survey_precisions(torch, flush, n_rep, f32_ms=None):
     return out
 
 
-def _case_lofar(torch, n_rep, peaks, tune=True, variant=None):
+def _case_lofar(torch, n_rep, peaks, tune=True, variant=None, n_out=None):
     """The paper's LOFAR instance (Section IV): 32 channels of 0.195 MHz from
     138 MHz, 5 us sampling, 2048 trial DMs 0-511.75, 200000 samples (1 s),
     FP32, unit weights. One DM step moves the lowest channel by ~900
@@ -471,6 +473,8 @@ def _case_lofar(torch, n_rep, peaks, tune=True, variant=None):
     from paper_1601_05052_gb300 import Plan
     g = torch.Generator(device="cuda")
     s = synth.setup("lofar")
+    if n_out:  # a shorter observation (smaller captures for profiling)
+        s = s.with_(n_out=n_out)
     p = Plan.from_setup(s)
     if variant:
         p.variant = variant
@@ -484,8 +488,8 @@ def _case_lofar(torch, n_rep, peaks, tune=True, variant=None):
     n_sm = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
     alu_peak = n_sm * 128 * peaks.get("sm_max_mhz", 2070.0) * 1e6
     comp = (x.numel() * 4 + o.numel() * 4) / (t * 1e-3)
-    return {"workload": "LOFAR: 32 ch (138-144.25 MHz, 5 us) x 2048 DM (0-511.75) x 200000 "
-                        "samples, FP32", "unit": UNIT,
+    return {"workload": "LOFAR: 32 ch (138-144.25 MHz, 5 us) x 2048 DM (0-511.75) x %d "
+                        "samples, FP32" % s.n_out, "unit": UNIT,
             "value": s.batch * s.n_dm * s.n_out / (t * 1e-3), "ms": t, "variant": p.variant,
             "gflops": adds / (t * 1e-3) / 1e9, "alu_frac": adds / (t * 1e-3) / alu_peak,
             "effective_hbm_gbs": comp / 1e9, "hbm_frac": comp / 1e9 / peaks["hbm_gbs"],
@@ -535,7 +539,7 @@ def run_only(args):
     elif args.only == "small_graph":
         out = _case_small_graph(torch, n, tune=tune)
     elif args.only == "lofar":
-        out = _case_lofar(torch, n, peaks, tune=tune, variant=variant)
+        out = _case_lofar(torch, n, peaks, tune=tune, variant=variant, n_out=args.n_out)
     elif args.only == "survey_precisions":
         out = _case_survey_precisions(torch, flush, n)
     else:

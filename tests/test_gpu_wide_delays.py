@@ -128,5 +128,11 @@ def test_lofar_full_size_sampled():
     got = out[0][torch.from_numpy(pd).cuda(), torch.from_numpy(pt).cuda()].cpu().numpy()
     ref, ab = points_by_beam(x, w, sh, pb, pd, pt, "f32")
     assert_float_parity(got, ref, ab, what="lofar %s" % plan.variant)
-    assert plan.variant["dm_per_thread"] * plan.variant["warps_dm"] >= 4, plan.variant
+    plan.check_device()
+    # a wide DM tile (its channel windows split per trial) on the same data
+    plan.variant = dict(kind=0, dm_per_thread=4, samples_per_thread=4, warps_dm=4, warps_time=2,
+                        chans_per_stage=4, stages=2)
+    out = plan.execute(to_dev(x, "f32"), weights_dev(w, "f32"))
+    got = out[0][torch.from_numpy(pd).cuda(), torch.from_numpy(pt).cuda()].cpu().numpy()
+    assert_float_parity(got, ref, ab, what="lofar %s" % plan.variant)
     plan.check_device()
