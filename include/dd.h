@@ -34,8 +34,9 @@
  *   - Threads. A plan may be used from several threads and streams at once
  *     for dd_execute. dd_adjoint and dd_execute_host use plan-owned device
  *     buffers, so their calls on one plan must be ordered (one stream, one
- *     thread at a time); dd_tune, dd_tune_adjoint and the set_variant calls
- *     must not run concurrently with other calls on the same plan.
+ *     thread at a time); dd_tune, dd_tune_adjoint, the set_variant calls and
+ *     dd_plan_set_launch_order must not run concurrently with other calls on
+ *     the same plan.
  */
 #ifndef DD_H_
 #define DD_H_
@@ -145,9 +146,24 @@ int32_t dd_plan_max_shift(dd_plan plan);
 dd_status dd_plan_shifts(dd_plan plan, int32_t *host_dst);
 
 /* Variant used by dd_execute. set: DD_ERR_ARG if the variant is not in the
- * compiled grid or does not fit the device's shared memory for this plan. */
+ * compiled grid or does not fit the device's shared memory for this plan;
+ * before it frees the old tables it waits (on the host) for this plan's
+ * earlier launches on every stream they went to, not for the whole device.
+ * After a launch of the plan was captured into a CUDA graph, replaced tables
+ * are kept until the plan is destroyed (the graph may still replay them). */
 dd_status dd_plan_get_variant(dd_plan plan, dd_variant *v);
 dd_status dd_plan_set_variant(dd_plan plan, const dd_variant *v);
+/* Launch order of the forward kernel's tiles: DM tiles fastest (the default;
+ * resident CTAs share a time range, so windows that neighbouring DM tiles
+ * share stay in L2) or time tiles fastest (resident CTAs sweep one DM tile's
+ * rows; better where neighbouring DM tiles read far-apart windows, e.g. the
+ * paper's LOFAR setup). dd_tune picks one for its winning variant;
+ * dd_plan_set_variant resets it to DM tiles fastest. Results do not depend
+ * on it. set: DD_ERR_ARG for another value. */
+#define DD_ORDER_DM_FASTEST 0
+#define DD_ORDER_TIME_FASTEST 1
+dd_status dd_plan_get_launch_order(dd_plan plan, int32_t *order);
+dd_status dd_plan_set_launch_order(dd_plan plan, int32_t order);
 /* Number of compiled variants and the i-th one (0 <= i < count). */
 int32_t dd_variant_count(void);
 dd_status dd_variant_get(int32_t i, dd_variant *v);
@@ -212,7 +228,9 @@ dd_status dd_grad_w_noalloc(dd_plan plan, const float *d_gout, const float *d_in
  * fills *rep (nullable). budget_ms bounds the sweep (0 = no bound).
  * Tuning cache: when the environment variable DD_TUNE_CACHE names a file,
  * dd_tune appends one text line "<key> kind dpt spt warps_dm warps_time
- * chans_per_stage stages" for the winner, the key being the device name,
+ * chans_per_stage stages order" for the winner (order: its launch order, see
+ * dd_plan_set_launch_order; a line without it means DM tiles fastest), the
+ * key being the device name,
  * input type, n_chan, n_dm, n_out, batch and a hash of the delay table; plan
  * creation (dd_plan_create, dd_plan_create_from_shifts) then starts from the
  * last line whose key matches, so the sweep is an offline step, as the paper
@@ -230,7 +248,9 @@ dd_status dd_tune_adjoint(dd_plan plan, int32_t budget_ms, dd_tune_report *rep);
  * (DD_ERR_UNSUPPORTED otherwise); both build the adjoint's buffers if they
  * do not exist yet. dd_adjoint_set_variant returns DD_ERR_ARG, leaving the
  * current variant in place, if v does not fit the transposed plan; it
- * synchronises the device (no launch may still read the old tables). */
+ * waits (on the host) for the transposed gather's own earlier launches, no
+ * launch of which may still read the old tables; other work on the device
+ * is not waited for. */
 dd_status dd_adjoint_get_variant(dd_plan plan, dd_variant *v);
 dd_status dd_adjoint_set_variant(dd_plan plan, const dd_variant *v);
 
@@ -250,14 +270,15 @@ dd_status dd_batch_create(dd_batch *out, int32_t n, const dd_plan *plans);
 dd_status dd_batch_execute(dd_batch batch, const void *const *d_in,
                            const void *const *d_w, void *const *d_out, void *stream);
 /* The batch's common variant; set gives every plan that variant and rebuilds
- * the tables and graph (synchronises the device). */
+ * the tables and graph, after waiting for the batch's own earlier launches
+ * (not the whole device). */
 dd_status dd_batch_get_variant(dd_batch batch, dd_variant *v);
 dd_status dd_batch_set_variant(dd_batch batch, const dd_variant *v);
 /* The variant plan i (index into the plans given to dd_batch_create) runs in
  * the batch. set changes only that plan's; DD_ERR_ARG, leaving every variant
  * as it was, if v does not share kind, dm_per_thread, samples_per_thread,
  * stages and warps_dm * warps_time with the other plans' or does not fit the
- * plan. Synchronises the device. */
+ * plan. Waits for the batch's own earlier launches (not the whole device). */
 dd_status dd_batch_get_plan_variant(dd_batch batch, int32_t i, dd_variant *v);
 dd_status dd_batch_set_plan_variant(dd_batch batch, int32_t i, const dd_variant *v);
 /* Auto-tunes a batch (Section IV-A's experiment applied to one launch):

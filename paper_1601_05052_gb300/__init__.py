@@ -140,6 +140,17 @@ class Plan:
         v = Variant(**d) if isinstance(d, dict) else Variant(*d)
         _lib.check(_lib_().dd_plan_set_variant(self._h, ctypes.byref(v)))
 
+    @property
+    def launch_order(self):
+        """'dm' (DM tiles fastest, the default) or 'time' (time tiles fastest)."""
+        o = ctypes.c_int32()
+        _lib.check(_lib_().dd_plan_get_launch_order(self._h, ctypes.byref(o)))
+        return "time" if o.value == 1 else "dm"
+
+    @launch_order.setter
+    def launch_order(self, order):
+        _lib.check(_lib_().dd_plan_set_launch_order(self._h, {"dm": 0, "time": 1}[order]))
+
     def tune(self, budget_ms=0):
         r = TuneReport()
         _lib.check(_lib_().dd_tune(self._h, int(budget_ms), ctypes.byref(r)))
@@ -299,6 +310,17 @@ class Batch:
     @property
     def plan_variants(self):
         return [self.plan_variant(i) for i in range(len(self.plans))]
+
+    @property
+    def launch_order(self):
+        """'dm' (DM tiles fastest, the default) or 'time' (time tiles fastest)."""
+        o = ctypes.c_int32()
+        _lib.check(_lib_().dd_plan_get_launch_order(self._h, ctypes.byref(o)))
+        return "time" if o.value == 1 else "dm"
+
+    @launch_order.setter
+    def launch_order(self, order):
+        _lib.check(_lib_().dd_plan_set_launch_order(self._h, {"dm": 0, "time": 1}[order]))
 
     def tune(self, budget_ms=0):
         r = TuneReport()

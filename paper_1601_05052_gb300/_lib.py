@@ -63,6 +63,8 @@ SIGNATURES = [
     ("dd_plan_shifts", i32, [P, P]),
     ("dd_plan_get_variant", i32, [P, ctypes.POINTER(Variant)]),
     ("dd_plan_set_variant", i32, [P, ctypes.POINTER(Variant)]),
+    ("dd_plan_get_launch_order", i32, [P, ctypes.POINTER(i32)]),
+    ("dd_plan_set_launch_order", i32, [P, i32]),
     ("dd_variant_count", i32, []),
     ("dd_variant_get", i32, [i32, ctypes.POINTER(Variant)]),
     ("dd_execute", i32, [P, P, P, P, P]),

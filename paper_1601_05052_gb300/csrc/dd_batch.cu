@@ -242,6 +242,10 @@ dd_status configure(dd_batch_s *bt, const std::vector<dd_variant> &pv) {
         a.bdesc = t.d_bdesc;
         a.n_blocks = t.n_blocks;
         a.ttile0 = 0;
+        a.dtile0 = 0;
+        a.grid_tt = t.n_ttiles;
+        a.grid_dt = t.n_dtiles;
+        a.time_major = 0;  // the persistent kernel orders its own work items
         a.p_elems = t.p_elems;
         a.live = nullptr;  // the persistent kernel sums every chunk
         a.err = p->d_err;

@@ -2,9 +2,13 @@
 //
 // Computes out[b][d][t] = sum_c w[c] * in[b][c][t + shift[d][c]] (Algorithm
 // 1, Section III-A, with weights) with one CTA per (DM tile, time tile,
-// beam); the tile body is in dd_fwd_tile.cuh. Grid x runs over DM tiles so
-// that CTAs resident at the same time share time ranges and the input
-// windows they stage stay in L2.
+// beam); the tile body is in dd_fwd_tile.cuh. By default the DM tile runs
+// fastest along grid x, so that CTAs resident at the same time share time
+// ranges and the input windows they stage stay in L2. Where neighbouring DM
+// tiles read far-apart windows (delays that grow by more than a time tile
+// per trial), the tuner can take the time tile fastest instead: resident
+// CTAs then sweep one DM tile's rows, and the next DM tile, whose windows
+// are shifted by a few DM steps, finds them still in L2.
 #include <algorithm>
 #include <atomic>
 
@@ -22,8 +26,11 @@ __global__ void __launch_bounds__(fwd_max_threads(KIND), fwd_min_blocks(KIND, DP
     uint64_t *bars = reinterpret_cast<uint64_t *>(smem);
     fwd_init_barriers<KIND>(bars, a.stages);
     uint32_t kbase = 0;
-    fwd_tile_any<KIND, T, DPT, SPT, LIVE>(a, a.dtile0 + int(blockIdx.x), a.ttile0 + int(blockIdx.y),
-                                          blockIdx.z, bars, smem + 128, kbase);
+    const int x = int(blockIdx.x);
+    const int dt = a.time_major ? x / a.grid_tt : x % a.grid_dt;
+    const int tt = a.time_major ? x % a.grid_tt : x / a.grid_dt;
+    fwd_tile_any<KIND, T, DPT, SPT, LIVE>(a, a.dtile0 + dt, a.ttile0 + tt, blockIdx.y, bars,
+                                          smem + 128, kbase);
 }
 
 // One CTA waits on an mbarrier that nothing arrives at, bounded by budget_ns.
@@ -173,7 +180,11 @@ dd_status launch_forward(dd_plan_s *p, const FwdTables &t, const void *in, const
     a.err = p->d_err;
     a.ttile0 = ttile0;
     a.dtile0 = dtile0;
-    dim3 grid(unsigned(n_dtiles), unsigned(n_ttiles), unsigned(p->B));
+    a.grid_tt = n_ttiles;
+    a.grid_dt = n_dtiles;
+    a.time_major = t.time_major ? 1 : 0;
+    if ((long long)n_dtiles * n_ttiles > 0x7fffffffLL) return fail(DD_ERR_ARG, "too many tiles");
+    dim3 grid(unsigned(n_dtiles * n_ttiles), unsigned(p->B));
     dim3 block(unsigned(32 * (t.v.warps_dm * t.v.warps_time + extra_warps(t.v.kind))));
     cudaError_t e = fn(a, grid, block, t.smem_bytes, st);
     if (e != cudaSuccess) return cuda_fail(e, "forward launch");

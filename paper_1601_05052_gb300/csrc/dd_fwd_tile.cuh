@@ -107,8 +107,10 @@ struct FwdArgs {
     int Dt, Ts, C_pad, cch, stages, warps_dm;
     int stage_data_bytes, stage_offs_bytes;
     int n_dtiles, n_ttiles, B;
-    int ttile0;  // one-shot launches: time tile of grid row 0 (a launch may cover a range)
-    int dtile0;  // one-shot launches: DM tile of grid column 0
+    // One-shot launches cover DM tiles [dtile0, dtile0 + grid_dt) by time
+    // tiles [ttile0, ttile0 + grid_tt); CTA x of the launch takes them with
+    // the DM tile fastest (time_major 0) or the time tile fastest (1).
+    int ttile0, dtile0, grid_tt, grid_dt, time_major;
     const int4 *copies;  // staging copies [n_dtiles][n_chunks][n_copies]
     int n_copies;
     const uint16_t *offs;
@@ -217,17 +219,14 @@ struct Stager {
     }
 
     // Warp-cooperative: stage chunk k into `slot`. Lane l issues the chunk's
-    // copies l, l + 32, ... (its first, `dsc`, preloaded), lane 0 also the
-    // tables and weights. All 32 lanes of one warp must call it.
+    // copy l (at most 32 per chunk; `dsc` preloaded), lane 0 also the tables
+    // and weights. All 32 lanes of one warp must call it.
     __device__ __forceinline__ void issue(int k, int slot, int4 dsc, uint64_t *full,
                                           int lane) const {
         unsigned char *sb = stage0 + slot * stage_bytes;
         const int c0 = (kc0 + k) * a.cch;
         const int nch = min(a.cch, a.C - c0);
-        const int4 *more = copies_k + (size_t)(kc0 + k) * a.n_copies;
-        uint32_t bytes = copy_bytes(dsc);
-        for (int m = lane + 32; m < a.n_copies; m += 32) bytes += copy_bytes(more[m]);
-        uint32_t total = bytes;
+        uint32_t total = copy_bytes(dsc);
 #pragma unroll
         for (int m = 16; m >= 1; m >>= 1) total += __shfl_xor_sync(0xffffffffu, total, m);
         const uint32_t w_bytes = uint32_t((nch * 4 + 15) & ~15);
@@ -235,7 +234,6 @@ struct Stager {
         __syncwarp();
         fence_proxy_async_smem();
         copy(sb, c0, dsc, full);
-        for (int m = lane + 32; m < a.n_copies; m += 32) copy(sb, c0, more[m], full);
         if (lane == 0) {
             unsigned char *tb = sb + a.stage_data_bytes;
             if (!subband) {

@@ -60,7 +60,8 @@ struct LaunchTracker {
 //                      win_len (elements, multiple of 16 bytes; 0 = none),
 //                      smem_off (element offset in the stage buffer),
 //                      channel - first channel of chunk j}
-//                     for the m-th copy of chunk j (capacity n_copies)
+//                     for the m-th copy of chunk j (capacity n_copies <= 32:
+//                     a variant whose chunks need more windows does not fit)
 //   offs[k][c][i] = smem element offset of sample t0 of trial k*Dt + i
 //                   in channel c (= smem_off + shift - win_start of its window)
 // Input segments of dd_execute_host's copy/compute pipeline.
@@ -77,6 +78,9 @@ struct FwdTables {
     size_t smem_bytes = 0;       // dynamic shared memory of one CTA
     int4 *d_copies = nullptr;    // [n_dtiles][n_chunks][n_copies]
     int n_copies = 0;
+    // launch order of the one-shot kernel: time tiles fastest (true) or DM
+    // tiles fastest (false, the default); chosen by dd_tune
+    bool time_major = false;
     uint16_t *d_offs = nullptr;
     // sub-band kinds only: d_offs holds per-group trial offsets into the
     // partial-sum buffer, [n_dtiles][C_pad/4][Dt]; d_bdesc the build blocks
@@ -192,7 +196,7 @@ bool aligned16(const void *p);
 // Tuning cache (DD_TUNE_CACHE): signature of a plan and a record of its
 // tuned variant.
 std::string plan_signature(const dd_plan_s *p);
-void cache_store(const std::string &key, const dd_variant &v);
+void cache_store(const std::string &key, const dd_variant &v, bool time_major);
 
 // Two-pass sweep of the variant grid (dd_tune.cpp). time_ms(v, &ms) sets ms
 // <= 0 for variants that do not fit; returns the fastest in *best.

@@ -207,7 +207,8 @@ dd_status build_fwd_tables(dd_plan_s *p, const dd_variant &v, FwdTables *out) {
     const int al = align_elems(p->dtype);
     const int elt = elt_bytes(p->dtype);
     const bool sb = is_subband(v.kind);
-    if (t.n_ttiles > 65535) return fail(DD_ERR_ARG, "too many time tiles for this variant");
+    if (int64_t(t.n_ttiles) * t.n_dtiles > 0x7fffffffLL)
+        return fail(DD_ERR_ARG, "too many tiles for this variant");
     if (sb && t.Dt % 8 != 0) return fail(DD_ERR_ARG, "sub-band variants need 8 | DM tile");
 
     const int G_pad = t.C_pad / kSbGroup;
@@ -340,9 +341,12 @@ dd_status build_fwd_tables(dd_plan_s *p, const dd_variant &v, FwdTables *out) {
             }
         }
     }
-    // staging copies with a common capacity (length-0 entries pad)
+    // staging copies with a common capacity (length-0 entries pad); one warp
+    // issues a chunk's copies, one per lane
     t.n_copies = 1;
     for (const auto &cl : copies) t.n_copies = std::max<int>(t.n_copies, int(cl.size()));
+    if (t.n_copies > 32)
+        return fail(DD_ERR_ARG, "more than 32 staging windows per chunk for this variant");
     std::vector<int4> copy_tab(copies.size() * size_t(t.n_copies), make_int4(0, 0, 0, 0));
     for (size_t i = 0; i < copies.size(); ++i)
         std::copy(copies[i].begin(), copies[i].end(), copy_tab.begin() + i * size_t(t.n_copies));
@@ -484,7 +488,10 @@ std::string plan_signature(const dd_plan_s *p) {
     return os.str();
 }
 
-bool cache_lookup(const std::string &key, dd_variant *v) {
+// Lines "<key> kind dpt spt warps_dm warps_time cch stages [time_major]"; a
+// line without the last field (written before the launch order was tuned)
+// means DM tiles fastest.
+bool cache_lookup(const std::string &key, dd_variant *v, bool *time_major) {
     const char *path = std::getenv("DD_TUNE_CACHE");
     if (!path || !*path) return false;
     std::ifstream f(path);
@@ -496,8 +503,11 @@ bool cache_lookup(const std::string &key, dd_variant *v) {
         dd_variant t{};
         if (is >> k >> t.kind >> t.dm_per_thread >> t.samples_per_thread >> t.warps_dm >>
             t.warps_time >> t.chans_per_stage >> t.stages) {
+            int tm = 0;
+            if (!(is >> tm)) tm = 0;
             if (k == key) {
                 *v = t;
+                *time_major = tm != 0;
                 found = true;
             }
         }
@@ -505,12 +515,13 @@ bool cache_lookup(const std::string &key, dd_variant *v) {
     return found;
 }
 
-void cache_store(const std::string &key, const dd_variant &v) {
+void cache_store(const std::string &key, const dd_variant &v, bool time_major) {
     const char *path = std::getenv("DD_TUNE_CACHE");
     if (!path || !*path) return;
     std::ofstream f(path, std::ios::app);
     f << key << " " << v.kind << " " << v.dm_per_thread << " " << v.samples_per_thread << " "
-      << v.warps_dm << " " << v.warps_time << " " << v.chans_per_stage << " " << v.stages << "\n";
+      << v.warps_dm << " " << v.warps_time << " " << v.chans_per_stage << " " << v.stages << " "
+      << (time_major ? 1 : 0) << "\n";
 }
 
 namespace {
@@ -544,7 +555,11 @@ dd_status finish_plan(dd_plan_s *p, dd_plan *out) {
 
     dd_status s = DD_ERR_UNSUPPORTED;
     dd_variant cached{};
-    if (cache_lookup(plan_signature(p), &cached)) s = build_fwd_tables(p, cached, &p->fwd);
+    bool cached_tm = false;
+    if (cache_lookup(plan_signature(p), &cached, &cached_tm)) {
+        s = build_fwd_tables(p, cached, &p->fwd);
+        if (s == DD_OK) p->fwd.time_major = cached_tm;
+    }
     for (size_t i = 0; s != DD_OK && i < sizeof(kDefaults) / sizeof(kDefaults[0]); ++i) {
         s = build_fwd_tables(p, kDefaults[i], &p->fwd);
         if (s != DD_OK && s != DD_ERR_ARG) return s;
@@ -689,6 +704,21 @@ dd_status dd_plan_set_variant(dd_plan p, const dd_variant *v) {
     dd_status s = build_fwd_tables(p, *v, &t);
     if (s != DD_OK) return s;
     return replace_fwd_tables(p, &p->fwd, t);  // waits for this plan's launches only
+}
+
+dd_status dd_plan_get_launch_order(dd_plan p, int32_t *order) {
+    if (!p || !order) return fail(DD_ERR_ARG, "null argument");
+    *order = p->fwd.time_major ? DD_ORDER_TIME_FASTEST : DD_ORDER_DM_FASTEST;
+    return DD_OK;
+}
+
+dd_status dd_plan_set_launch_order(dd_plan p, int32_t order) {
+    if (!p) return fail(DD_ERR_ARG, "null plan");
+    if (order != DD_ORDER_DM_FASTEST && order != DD_ORDER_TIME_FASTEST)
+        return fail(DD_ERR_ARG, "launch order must be DD_ORDER_DM_FASTEST or DD_ORDER_TIME_FASTEST");
+    std::lock_guard<std::mutex> lk(p->mu);
+    p->fwd.time_major = order == DD_ORDER_TIME_FASTEST;  // read at each launch; tables unchanged
+    return DD_OK;
 }
 
 // The variant grid: every compiled (kind, dm_per_thread, samples_per_thread)
