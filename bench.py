@@ -73,6 +73,8 @@ def _args():
     ap.add_argument("--variant", default=None,
                     help="with --only uneven_*/f32_96beams: JSON forward variant to use instead "
                          "of tuning (e.g. one a tuned run printed)")
+    ap.add_argument("--dtype", choices=["f32", "f16", "bf16", "u8"], default=None,
+                    help="with --only survey_precisions: that input type alone")
     ap.add_argument("--n-out", type=int, default=None,
                     help="with --only lofar: output samples (default: the full 200000)")
     ap.add_argument("--tune-ms", type=int, default=0,
@@ -434,7 +436,8 @@ def _case_differentiable(torch, flush, n_rep, tune=True):
             "variant": p.variant, "adjoint_variant": rep_adj["best"] if rep_adj else None}
 
 
-def _case_survey_precisions(torch, flush, n_rep, f32_ms=None):
+def _case_survey_precisions(torch, flush, n_rep, f32_ms=None,
+                            dtypes=("f32", "f16", "bf16", "u8")):
     """The survey workload (1 beam x 1024 ch x 2048 DM x 20000) with 16-bit
     and 8-bit input against FP32, each in its default variant."""
     import synth
@@ -443,7 +446,7 @@ def _case_survey_precisions(torch, flush, n_rep, f32_ms=None):
     s = synth.setup(WORKLOAD)
     units = s.batch * s.n_dm * s.n_out
     out = {"workload": "survey scale, default variant per input type", "unit": UNIT}
-    for dtype in ("f32", "f16", "bf16", "u8"):
+    for dtype in dtypes:
         if dtype == "f32" and f32_ms is not None:
             out["f32"] = units / (f32_ms * 1e-3)
             continue
@@ -457,8 +460,9 @@ def _case_survey_precisions(torch, flush, n_rep, f32_ms=None):
         out[dtype + "_variant"] = p.variant
         del x, o
         p.close()
-    for dtype in ("f16", "bf16", "u8"):
-        out["speedup_%s_vs_f32" % dtype] = out[dtype] / out["f32"]
+    for dtype in dtypes:
+        if dtype != "f32" and "f32" in out:
+            out["speedup_%s_vs_f32" % dtype] = out[dtype] / out["f32"]
     return out
 
 
@@ -549,7 +553,9 @@ def run_only(args):
     elif args.only == "lofar":
         out = _case_lofar(torch, n, peaks, tune=tune, variant=variant, n_out=args.n_out)
     elif args.only == "survey_precisions":
-        out = _case_survey_precisions(torch, flush, n)
+        out = _case_survey_precisions(torch, flush, n,
+                                      dtypes=(args.dtype,) if args.dtype else
+                                      ("f32", "f16", "bf16", "u8"))
     else:
         out = _case_differentiable(torch, flush, n, tune=tune)
     print(json.dumps({"case": args.only, "steps": n, **out}), flush=True)

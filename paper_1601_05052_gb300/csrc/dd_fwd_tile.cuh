@@ -441,7 +441,7 @@ __device__ __forceinline__ void fwd_tile(const FwdArgs &a, int dtile, int ttile,
     const Stager<T> st = make_stager<T>(a, dtile, b, t0, stage0, false, kr.x);
 
     // warp 0 stages chunk k, after the slot's previous chunk was released;
-    // once the CTA has given up a wait it issues nothing more
+    // once a wait of the CTA has given up it issues nothing more
     auto issue = [&](int k, int4 dsc) {
         const uint32_t kg = kbase + uint32_t(k);
         const int slot = int(kg % S);
@@ -449,7 +449,7 @@ __device__ __forceinline__ void fwd_tile(const FwdArgs &a, int dtile, int ttile,
         if (kg >= S)
             ok = mbar_wait_bounded(&empty[slot], ((kg / S) - 1u) & 1u, a.err, kWaitBudgetNs,
                                    gave_up);
-        if (__all_sync(0xffffffffu, ok && !*gave_up)) st.issue(k, slot, dsc, &full[slot], lane);
+        if (__all_sync(0xffffffffu, ok)) st.issue(k, slot, dsc, &full[slot], lane);
     };
     if (warp == 0) {
         const int pro = min(int(S), n_chunks);
