@@ -130,7 +130,7 @@ def test_lofar_full_size_sampled():
     assert_float_parity(got, ref, ab, what="lofar %s" % plan.variant)
     plan.check_device()
     # a wide DM tile (its channel windows split per trial) on the same data
-    plan.variant = dict(kind=0, dm_per_thread=4, samples_per_thread=4, warps_dm=4, warps_time=2,
+    plan.variant = dict(kind=0, dm_per_thread=4, samples_per_thread=4, warps_dm=2, warps_time=4,
                         chans_per_stage=4, stages=2)
     out = plan.execute(to_dev(x, "f32"), weights_dev(w, "f32"))
     got = out[0][torch.from_numpy(pd).cuda(), torch.from_numpy(pt).cuda()].cpu().numpy()
