@@ -417,89 +417,6 @@ __device__ __forceinline__ void fwd_init_barriers(uint64_t *bars, int stages) {
     __syncthreads();
 }
 
-// 8-bit input whose channel weights are all 0 or one common value w0 (unit
-// weights, RFI masks, a common Q8 scale): every warp scans the C weights.
-// Then out = w0 * sum over the weighted channels of x, and the sums of raw
-// bytes can be taken four samples per 32-bit word (see ByteQuads). Weights
-// of other values take the general path.
-__device__ __forceinline__ bool mask_weights(const FwdArgs &a, int lane, int *w0) {
-    const int *w = static_cast<const int *>(a.w);
-    int first = 0;
-    bool ok = true;
-    for (int c0 = 0; c0 < a.C; c0 += 32) {
-        const int v = c0 + lane < a.C ? __ldg(w + c0 + lane) : 0;
-        const unsigned nz = __ballot_sync(0xffffffffu, v != 0);
-        if (first == 0 && nz) first = __shfl_sync(0xffffffffu, v, __ffs(nz) - 1);
-        ok = ok && (v == 0 || v == first);
-    }
-    *w0 = first;
-    return __all_sync(0xffffffffu, ok);
-}
-
-// Sums of raw bytes four samples at a time (8-bit input, mask weights;
-// kinds 0 and 5 with samples_per_thread a multiple of 4). Lane l owns the
-// samples 4l + 128q + k (k < 4) of its warp's time range. It reads the four
-// bytes of a trial's samples with one 32-bit shared load (two and a byte
-// permute when the trial's offset is not a multiple of 4; the offset's
-// remainder is the same for the whole warp) and adds them as two words of
-// 16-bit lanes: bytes 0 and 2 into `ev`, bytes 1 and 3 into `od`. A 16-bit
-// lane holds the sum of up to 257 bytes, so every 256 weighted channels the
-// lanes move into the 32-bit totals.
-template <int DPT, int SPT, bool REUSE>
-struct ByteQuads {
-    static constexpr int Q = SPT / 4;
-    static constexpr int kSpill = 256;
-    uint32_t ev[DPT][Q], od[DPT][Q];
-    int n = 0;  // channels summed into the 16-bit lanes since the last move
-
-    __device__ __forceinline__ void clear() {
-#pragma unroll
-        for (int i = 0; i < DPT; ++i)
-#pragma unroll
-            for (int q = 0; q < Q; ++q) ev[i][q] = od[i][q] = 0u;
-        n = 0;
-    }
-    __device__ __forceinline__ void spill(int (&acc)[DPT][SPT]) {
-#pragma unroll
-        for (int i = 0; i < DPT; ++i)
-#pragma unroll
-            for (int q = 0; q < Q; ++q) {
-                acc[i][4 * q + 0] += int(ev[i][q] & 0xffffu);
-                acc[i][4 * q + 2] += int(ev[i][q] >> 16);
-                acc[i][4 * q + 1] += int(od[i][q] & 0xffffu);
-                acc[i][4 * q + 3] += int(od[i][q] >> 16);
-            }
-        clear();
-    }
-    // one channel: s32 = the staged chunk as words, wl = this lane's word
-    // index relative to a trial's offset (its time base / 4)
-    __device__ __forceinline__ void channel(int (&acc)[DPT][SPT], const uint32_t *s32, int wl,
-                                            const int (&o)[DPT]) {
-        uint32_t x[Q];
-#pragma unroll
-        for (int i = 0; i < DPT; ++i) {
-            if (!REUSE || i == 0 || o[i] != o[i - 1]) {
-                const uint32_t *src = s32 + (o[i] >> 2) + wl;
-                const int r = o[i] & 3;
-                if (r == 0) {
-#pragma unroll
-                    for (int q = 0; q < Q; ++q) x[q] = src[32 * q];
-                } else {
-                    const uint32_t sel = 0x3210u + 0x1111u * uint32_t(r);
-#pragma unroll
-                    for (int q = 0; q < Q; ++q) x[q] = __byte_perm(src[32 * q], src[32 * q + 1], sel);
-                }
-            }
-#pragma unroll
-            for (int q = 0; q < Q; ++q) {
-                ev[i][q] += __byte_perm(x[q], 0u, 0x4240u);
-                od[i][q] += __byte_perm(x[q], 0u, 0x4341u);
-            }
-        }
-        if (++n == kSpill) spill(acc);
-    }
-};
-
 // Kinds 0, 1 and 5. `kbase` counts the chunks this CTA has already pushed
 // through its slots; chunk kg uses slot kg % stages, and the n-th completion
 // of a slot's full/empty barrier belongs to chunk slot + n * stages, so the
@@ -539,86 +456,46 @@ __device__ __forceinline__ void fwd_tile(const FwdArgs &a, int dtile, int ttile,
         for (int k = 0; k < pro; ++k) issue(k, st.desc(k, lane));
     }
 
-    // The chunk loop; body(sb, soffs, sw, nch) sums one staged chunk.
-    auto chunks = [&](auto &&body) {
-        for (int k = 0; k < n_chunks; ++k) {
-            const uint32_t kg = kbase + uint32_t(k);
-            const int slot = int(kg % S);
-            const int kn = k - 1 + int(S);  // the chunk warp 0 stages after this one
-            int4 pre = make_int4(0, 0, 0, 0);
-            if (warp == 0 && k >= 1 && kn < n_chunks) pre = st.desc(kn, lane);
-            // A failed wait (or one that finds the CTA's give-up flag set)
-            // ends the tile: the slot may hold a stale chunk, so nothing more
-            // is summed, released or stored.
-            if (!__all_sync(0xffffffffu, mbar_wait_bounded(&full[slot], (kg / S) & 1u, a.err,
-                                                           kWaitBudgetNs, gave_up)))
-                break;
-            const unsigned char *sb = stage0 + slot * st.stage_bytes;
-            const uint16_t *soffs =
-                reinterpret_cast<const uint16_t *>(sb + a.stage_data_bytes) + wd * DPT;
-            const Wt *sw = reinterpret_cast<const Wt *>(sb + a.stage_data_bytes + st.tab_bytes);
-            body(sb, soffs, sw, min(a.cch, a.C - (kr.x + k) * a.cch));
-            __syncwarp();
-            if (lane == 0) mbar_arrive(&empty[slot]);
-            // refill the slot of the previous chunk (one chunk of slack for
-            // the other warps), keeping stages-1 chunks in flight
-            if (warp == 0 && k >= 1 && kn < n_chunks) issue(kn, pre);
-        }
-        kbase += uint32_t(n_chunks);
-    };
-
     Acc acc[DPT][SPT];
 #pragma unroll
     for (int i = 0; i < DPT; ++i)
 #pragma unroll
         for (int j = 0; j < SPT; ++j) acc[i][j] = Acc(0);
-    Acc *out = static_cast<Acc *>(a.out);
-
-    if constexpr (std::is_same<T, uint8_t>::value && KIND != 1 && SPT % 4 == 0) {
-        int w0 = 0;
-        if (mask_weights(a, lane, &w0)) {
-            ByteQuads<DPT, SPT, KIND == 5> bq;
-            bq.clear();
-            const int wl = wt * 8 * SPT + lane;  // (time base of lane) / 4
-            chunks([&](const unsigned char *sb, const uint16_t *soffs, const int *sw, int nch) {
-                const uint32_t *s32 = reinterpret_cast<const uint32_t *>(sb);
-                for (int cc = 0; cc < nch; ++cc) {
-                    if (sw[cc] == 0) continue;  // a masked channel adds nothing
-                    int o[DPT];
-                    load_offsets<DPT>(soffs + cc * a.Dt, o);
-                    bq.channel(acc, s32, wl, o);
-                }
-            });
-            if (*gave_up) return;
-            bq.spill(acc);
-            const int lb4 = 4 * wl;
-#pragma unroll
-            for (int i = 0; i < DPT; ++i) {
-                const int d = dtile * a.Dt + wd * DPT + i;
-                if (d >= a.D) continue;
-                int *orow = out + ((long long)b * a.D + d) * a.S + t0 + lb4;
-                const long long tmax = a.S - t0 - lb4;
-#pragma unroll
-                for (int q = 0; q < SPT / 4; ++q)
-#pragma unroll
-                    for (int k = 0; k < 4; ++k)
-                        if (128 * q + k < tmax) orow[128 * q + k] = w0 * acc[i][4 * q + k];
-            }
-            return;
-        }
-    }
-
     const int lb = P::lane_base(wt, lane);
-    chunks([&](const unsigned char *sb, const uint16_t *soffs, const Wt *sw, int nch) {
+
+    for (int k = 0; k < n_chunks; ++k) {
+        const uint32_t kg = kbase + uint32_t(k);
+        const int slot = int(kg % S);
+        const int kn = k - 1 + int(S);  // the chunk warp 0 stages after this one
+        int4 pre = make_int4(0, 0, 0, 0);
+        if (warp == 0 && k >= 1 && kn < n_chunks) pre = st.desc(kn, lane);
+        // A failed wait (or one that finds the CTA's give-up flag set) ends
+        // the tile: the slot may hold a stale chunk, so nothing more is
+        // summed, released or stored.
+        if (!__all_sync(0xffffffffu, mbar_wait_bounded(&full[slot], (kg / S) & 1u, a.err,
+                                                       kWaitBudgetNs, gave_up)))
+            break;
+        const unsigned char *sb = stage0 + slot * st.stage_bytes;
         const T *sdata = reinterpret_cast<const T *>(sb);
+        const uint16_t *soffs =
+            reinterpret_cast<const uint16_t *>(sb + a.stage_data_bytes) + wd * DPT;
+        const Wt *sw = reinterpret_cast<const Wt *>(sb + a.stage_data_bytes + st.tab_bytes);
+        const int nch = min(a.cch, a.C - (kr.x + k) * a.cch);
         for (int cc = 0; cc < nch; ++cc) {
             int o[DPT];
             load_offsets<DPT>(soffs + cc * a.Dt, o);
             P::channel(acc, sdata, lb, o, sw[cc]);
         }
-    });
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&empty[slot]);
+        // refill the slot of the previous chunk (one chunk of slack for the
+        // other warps), keeping stages-1 chunks in flight
+        if (warp == 0 && k >= 1 && kn < n_chunks) issue(kn, pre);
+    }
+    kbase += uint32_t(n_chunks);
     if (*gave_up) return;
 
+    Acc *out = static_cast<Acc *>(a.out);
 #pragma unroll
     for (int i = 0; i < DPT; ++i) {
         const int d = dtile * a.Dt + wd * DPT + i;
@@ -768,190 +645,6 @@ __device__ __forceinline__ void sb_trials(Acc (&acc)[DPT][SPT], const Acc *Pl,
     }
 }
 
-// Sub-band partial series of 8-bit input with mask weights (see
-// mask_weights): an element is the unweighted sum of the group's weighted
-// channels, at most 4 * 255 < 2^10, so two elements 32 apart share one word,
-// W[u] = P[u] | P[u + 32] << 16, and the lane-strided trial loop reads a
-// lane's samples u and u + 32 with one 32-bit load. A block's lane holds
-// P[u0 + 32q + l] for its sub-blocks q, so it writes the words of all but
-// the last sub-block whole, the low half of the last one's, and the high
-// half of the word 32 before its first (unless the block starts a series;
-// descriptor bit 27); the block before it writes that word's low half.
-__device__ __forceinline__ void sb_build_blocks_packed(uint32_t *W, const uint8_t *raw,
-                                                       const int4 *blk, const int *sw,
-                                                       int n_blocks, int part, int parts,
-                                                       int lane) {
-    uint16_t *W16 = reinterpret_cast<uint16_t *>(W);
-    int b = part;
-    int4 d = b < n_blocks ? blk[b] : make_int4(0, 0, 0, 0);
-    while (b < n_blocks) {
-        const int bn = b + parts;
-        const int4 dn = bn < n_blocks ? blk[bn] : make_int4(0, 0, 0, 0);
-        const int nsub = (d.w >> 24) & 7;
-        if (!nsub) break;
-        {
-            const int g = (d.w >> 16) & 3, gn = (d.w >> 20) & 7;
-            const int4 wv = *reinterpret_cast<const int4 *>(sw + 4 * g);
-            const bool use[4] = {wv.x != 0, gn > 1 && wv.y != 0, gn > 2 && wv.z != 0,
-                                 gn > 3 && wv.w != 0};
-            const int r0 = d.y + lane;
-            const int r[4] = {r0, r0 + int(short(d.z & 0xffff)), r0 + (d.z >> 16),
-                              r0 + int(short(d.w & 0xffff))};
-            uint32_t v[4] = {0u, 0u, 0u, 0u};
-#pragma unroll
-            for (int j = 0; j < 4; ++j)
-                if (use[j]) {
-#pragma unroll
-                    for (int q = 0; q < 4; ++q)
-                        if (q < nsub) v[q] += raw[r[j] + 32 * q];
-                }
-#pragma unroll
-            for (int q = 0; q < 4; ++q) {
-                if (q + 1 < nsub) W[d.x + 32 * q + lane] = v[q] | (v[q + 1] << 16);
-                else if (q + 1 == nsub) W16[2 * (d.x + 32 * q + lane)] = uint16_t(v[q]);
-            }
-            if (!((d.w >> 27) & 1)) W16[2 * (d.x - 32 + lane) + 1] = uint16_t(v[0]);
-        }
-        d = dn;
-        b = bn;
-    }
-}
-
-// Moves the 16-bit lane sums of the packed trial loop into the 32-bit totals.
-template <int DPT, int SPT, typename Acc, typename Accp>
-__device__ __forceinline__ void packed_spill(Acc (&acc)[DPT][SPT], Accp &accp) {
-#pragma unroll
-    for (int i = 0; i < DPT; ++i)
-#pragma unroll
-        for (int m = 0; m < SPT / 2; ++m) {
-            acc[i][2 * m] += Acc(accp[i][m] & 0xffffu);
-            acc[i][2 * m + 1] += Acc(accp[i][m] >> 16);
-            accp[i][m] = 0u;
-        }
-}
-
-// The trial loop over packed series: accp[i][m] gathers, in 16-bit lanes,
-// samples 64m (low) and 64m + 32 (high) of trial i relative to the lane.
-template <int DPT, int SPT>
-__device__ __forceinline__ void sb_trials_packed(uint32_t (&accp)[DPT][SPT / 2],
-                                                 const uint32_t *Wl, const uint16_t *poffs,
-                                                 int Dt, int ng) {
-    OffWords<DPT> ow[4];
-#pragma unroll
-    for (int g = 0; g < 4; ++g)
-        if (g < ng) ow[g] = load_offwords<DPT>(poffs + g * Dt);
-#pragma unroll
-    for (int g = 0; g < 4; ++g) {
-        if (g < ng) {
-            int o[DPT];
-#pragma unroll
-            for (int i = 0; i < DPT / 2; ++i) {
-                o[2 * i] = int(ow[g].w[i] & 0xffffu);
-                o[2 * i + 1] = int(ow[g].w[i] >> 16);
-            }
-            uint32_t v[SPT / 2];
-#pragma unroll
-            for (int i = 0; i < DPT; ++i) {
-                if (i == 0 || o[i] != o[i - 1]) {
-#pragma unroll
-                    for (int m = 0; m < SPT / 2; ++m) v[m] = Wl[o[i] + 64 * m];
-                }
-#pragma unroll
-                for (int m = 0; m < SPT / 2; ++m) accp[i][m] += v[m];
-            }
-        }
-    }
-}
-
-// The compute warps of the sub-band kinds 2 and 4 (see fwd_tile_sb). PACKED:
-// 8-bit input with mask weights, packed series (sb_build_blocks_packed) and
-// 16-bit lane sums that move into the 32-bit totals every 64 groups (64 *
-// 1020 < 2^16); the totals are scaled by the common weight w0 at the end.
-template <typename T, int DPT, int SPT, bool LIVE, bool PACKED>
-__device__ __forceinline__ void sb_compute(const FwdArgs &a, const Stager<T> &st, int dtile,
-                                           int b, long long t0, int2 kr, uint64_t *bars,
-                                           unsigned char *pslot0, int pslot_bytes,
-                                           uint32_t &kbase, int w0) {
-    using Acc = typename Elem<T>::Acc;
-    using Wt = typename Elem<T>::W;
-    uint64_t *full = bars, *empty = bars + 8;
-    volatile int *gave_up = reinterpret_cast<volatile int *>(&bars[7]);
-    const uint32_t S = uint32_t(a.stages);
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const int nc = int(blockDim.x >> 5) - 1;
-    const int n_chunks = kr.y - kr.x;
-    const uint32_t poffs_bytes = st.tab1_bytes;
-    const int wd = warp % a.warps_dm, wt = warp / a.warps_dm;
-    Acc acc[DPT][SPT];
-#pragma unroll
-    for (int i = 0; i < DPT; ++i)
-#pragma unroll
-        for (int j = 0; j < SPT; ++j) acc[i][j] = Acc(0);
-    uint32_t accp[PACKED ? DPT : 1][SPT / 2];
-    if constexpr (PACKED) {
-#pragma unroll
-        for (int i = 0; i < DPT; ++i)
-#pragma unroll
-            for (int m = 0; m < SPT / 2; ++m) accp[i][m] = 0u;
-    }
-    int groups = 0;
-    const int lb = wt * 32 * SPT + lane;
-
-    for (int k = 0; k < n_chunks; ++k) {
-        const uint32_t kg = kbase + uint32_t(k);
-        const int slot = int(kg % S);
-        // A failed wait sets the give-up flag before the barrier; after it
-        // every warp sees the flag and skips the trials on the chunk.
-        const bool ok = __all_sync(
-            0xffffffffu,
-            mbar_wait_bounded(&full[slot], (kg / S) & 1u, a.err, kWaitBudgetNs, gave_up));
-        const unsigned char *sb = st.stage0 + slot * st.stage_bytes;
-        const T *raw = reinterpret_cast<const T *>(sb);
-        const int4 *bd = reinterpret_cast<const int4 *>(sb + a.stage_data_bytes + poffs_bytes);
-        const Wt *sw = reinterpret_cast<const Wt *>(sb + a.stage_data_bytes + st.tab_bytes);
-        unsigned char *pb = pslot0 + (kg & 1u) * pslot_bytes;
-        Acc *P = reinterpret_cast<Acc *>(pb);
-        uint16_t *poffs = reinterpret_cast<uint16_t *>(pb + a.p_elems * int(sizeof(Acc)));
-        const int ng = (min(a.cch, a.C - (kr.x + k) * a.cch) + kSbG - 1) / kSbG;
-
-        if (ok) {
-            if constexpr (PACKED)
-                sb_build_blocks_packed(reinterpret_cast<uint32_t *>(P), raw, bd, sw, a.n_blocks,
-                                       warp, nc, lane);
-            else
-                sb_build_blocks<T>(P, raw, bd, sw, a.n_blocks, warp, nc, lane);
-            // the chunk's trial offsets move next to its partial sums
-            const uint32_t *src = reinterpret_cast<const uint32_t *>(sb + a.stage_data_bytes);
-            uint32_t *dst = reinterpret_cast<uint32_t *>(poffs);
-            for (int i = tid; i < int(poffs_bytes / 4); i += nc * 32) dst[i] = src[i];
-        }
-        compute_barrier(nc * 32);
-        if (*gave_up) continue;  // no arrival: the producer's next wait fails too
-        if (tid == 0) mbar_arrive(&empty[slot]);  // nothing reads this staging slot any more
-        if constexpr (PACKED) {
-            if (groups + ng > 64) {
-                packed_spill<DPT, SPT>(acc, accp);
-                groups = 0;
-            }
-            groups += ng;
-            sb_trials_packed<DPT, SPT>(accp, reinterpret_cast<const uint32_t *>(P) + lb,
-                                       poffs + wd * DPT, a.Dt, ng);
-        } else {
-            sb_trials<Acc, DPT, SPT>(acc, P + lb, poffs + wd * DPT, a.Dt, ng);
-        }
-    }
-    kbase += uint32_t(n_chunks);
-    if (*gave_up) return;
-    if constexpr (PACKED) {
-        packed_spill<DPT, SPT>(acc, accp);
-#pragma unroll
-        for (int i = 0; i < DPT; ++i)
-#pragma unroll
-            for (int j = 0; j < SPT; ++j) acc[i][j] *= w0;
-    }
-    store_lane_strided<Acc, DPT, SPT>(a, acc, dtile, b, t0, wd, lb);
-}
-
 // kind 2: sub-band partial sums with a producer warp. Warps [0, NC) compute;
 // warp NC only stages chunks, running up to `stages` chunks ahead and
 // throttled by the slots' empty barriers (one arrival per chunk, made after
@@ -1016,16 +709,45 @@ __device__ __forceinline__ void fwd_tile_sb(const FwdArgs &a, int dtile, int tti
     }
 
     // ---------------- compute warps
-    if constexpr (std::is_same<T, uint8_t>::value && SPT % 2 == 0) {
-        int w0 = 0;
-        if (mask_weights(a, lane, &w0)) {
-            sb_compute<T, DPT, SPT, LIVE, true>(a, st, dtile, b, t0, kr, bars, pslot0, pslot_bytes,
-                                                kbase, w0);
-            return;
+    const int wd = warp % a.warps_dm, wt = warp / a.warps_dm;
+    Acc acc[DPT][SPT];
+#pragma unroll
+    for (int i = 0; i < DPT; ++i)
+#pragma unroll
+        for (int j = 0; j < SPT; ++j) acc[i][j] = Acc(0);
+    const int lb = wt * 32 * SPT + lane;
+
+    for (int k = 0; k < n_chunks; ++k) {
+        const uint32_t kg = kbase + uint32_t(k);
+        const int slot = int(kg % S);
+        // A failed wait sets the give-up flag before the barrier; after it
+        // every warp sees the flag and skips the trials on the chunk.
+        const bool ok = __all_sync(
+            0xffffffffu,
+            mbar_wait_bounded(&full[slot], (kg / S) & 1u, a.err, kWaitBudgetNs, gave_up));
+        const unsigned char *sb = stage0 + slot * st.stage_bytes;
+        const T *raw = reinterpret_cast<const T *>(sb);
+        const int4 *bd = reinterpret_cast<const int4 *>(sb + a.stage_data_bytes + poffs_bytes);
+        const Wt *sw = reinterpret_cast<const Wt *>(sb + a.stage_data_bytes + st.tab_bytes);
+        unsigned char *pb = pslot0 + (kg & 1u) * pslot_bytes;
+        Acc *P = reinterpret_cast<Acc *>(pb);
+        uint16_t *poffs = reinterpret_cast<uint16_t *>(pb + a.p_elems * int(sizeof(Acc)));
+        const int ng = (min(a.cch, a.C - (kr.x + k) * a.cch) + kSbG - 1) / kSbG;
+
+        if (ok) {
+            sb_build_blocks<T>(P, raw, bd, sw, a.n_blocks, warp, nc, lane);
+            // the chunk's trial offsets move next to its partial sums
+            const uint32_t *src = reinterpret_cast<const uint32_t *>(sb + a.stage_data_bytes);
+            uint32_t *dst = reinterpret_cast<uint32_t *>(poffs);
+            for (int i = tid; i < int(poffs_bytes / 4); i += nc * 32) dst[i] = src[i];
         }
+        compute_barrier(nc * 32);
+        if (*gave_up) continue;  // no arrival: the producer's next wait fails too
+        if (tid == 0) mbar_arrive(&empty[slot]);  // nothing reads this staging slot any more
+        sb_trials<Acc, DPT, SPT>(acc, P + lb, poffs + wd * DPT, a.Dt, ng);
     }
-    sb_compute<T, DPT, SPT, LIVE, false>(a, st, dtile, b, t0, kr, bars, pslot0, pslot_bytes, kbase,
-                                         1);
+    kbase += uint32_t(n_chunks);
+    if (!*gave_up) store_lane_strided<Acc, DPT, SPT>(a, acc, dtile, b, t0, wd, lb);
 }
 
 // kind 3: warp-specialised sub-band. Warps [0, NC) are trial warps (as in

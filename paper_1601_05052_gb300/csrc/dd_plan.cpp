@@ -308,8 +308,7 @@ dd_status build_fwd_tables(dd_plan_s *p, const dd_variant &v, FwdTables *out) {
                 const int ng = int(ch.poffs.size()) / t.Dt;
                 // Build blocks: every partial series is cut into blocks of up
                 // to 4 x 32 elements, {dst, r0, (r1-r0) | (r2-r0) << 16, (r3-r0)
-                // | group << 16 | channels << 20 | sub-blocks << 24 | first
-                // block of its series << 27} with the
+                // | group << 16 | channels << 20 | sub-blocks << 24} with the
                 // relative offsets as int16 (lane l of sub-block s builds
                 // dst[32 s + l] = sum_j w_j raw[r_j + 32 s + l]); the series'
                 // buffer lengths are whole 32-element sub-blocks, so no lane
@@ -335,8 +334,7 @@ dd_status build_fwd_tables(dd_plan_s *p, const dd_variant &v, FwdTables *out) {
                                 bd[0] + u, bd[2] + u,
                                 int((uint32_t(rel[1]) & 0xffffu) | (uint32_t(rel[2]) << 16)),
                                 int((uint32_t(rel[3]) & 0xffffu) | (uint32_t(g) << 16) |
-                                    (uint32_t(gn) << 20) | (uint32_t(nsub) << 24) |
-                                    (u == 0 ? 1u << 27 : 0u))));
+                                    (uint32_t(gn) << 20) | (uint32_t(nsub) << 24))));
                         }
                     }
                 }
