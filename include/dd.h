@@ -91,7 +91,7 @@ typedef struct {
     int32_t samples_per_thread;  /* samples accumulated per thread          */
     int32_t warps_dm;            /* warps along the DM axis of a CTA        */
     int32_t warps_time;          /* warps along the time axis of a CTA      */
-    int32_t chans_per_stage;     /* channels staged per pipeline stage      */
+    int32_t chans_per_stage;     /* channels per pipeline stage: 4, 8, 16, 32 */
     int32_t stages;              /* shared-memory pipeline depth (2..4)     */
 } dd_variant;
 

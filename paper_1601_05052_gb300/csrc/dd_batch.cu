@@ -520,7 +520,7 @@ dd_status dd_batch_tune(dd_batch bt, int32_t budget_ms, dd_tune_report *rep) {
         for (size_t j = 0; j < n && s == DD_OK && cur > 0 && !over(); ++j) {
             for (int wdm = 1; wdm <= tw && s == DD_OK; ++wdm) {
                 if (tw % wdm) continue;
-                for (int cch : {4, 8, 16}) {
+                for (int cch : {4, 8, 16, 32}) {
                     std::vector<dd_variant> cand = pv;
                     cand[j].warps_dm = wdm;
                     cand[j].warps_time = tw / wdm;

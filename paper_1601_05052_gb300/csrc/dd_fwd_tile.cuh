@@ -537,7 +537,7 @@ __device__ __forceinline__ void sb_build_blocks(typename Elem<T>::Acc *P, const 
         const int nsub = (d.w >> 24) & 7;
         if (!nsub) break;
         {
-            const int g = (d.w >> 16) & 3, gn = (d.w >> 20) & 7;
+            const int g = (d.w >> 16) & 7, gn = (d.w >> 20) & 7;
             const int4 wv = *reinterpret_cast<const int4 *>(sw + 4 * g);
             const Wt w[4] = {__builtin_bit_cast(Wt, wv.x), __builtin_bit_cast(Wt, wv.y),
                              __builtin_bit_cast(Wt, wv.z), __builtin_bit_cast(Wt, wv.w)};
@@ -607,14 +607,14 @@ __device__ __forceinline__ OffWords<DPT> load_offwords(const uint16_t *p) {
 }
 
 template <typename Acc, int DPT, int SPT>
-__device__ __forceinline__ void sb_trials(Acc (&acc)[DPT][SPT], const Acc *Pl,
-                                          const uint16_t *poffs, int Dt, int ng) {
+__device__ __forceinline__ void sb_trials4(Acc (&acc)[DPT][SPT], const Acc *Pl,
+                                           const uint16_t *poffs, int Dt, int ng) {
     OffWords<DPT> ow[4];
 #pragma unroll
     for (int g = 0; g < 4; ++g)
         if (g < ng) ow[g] = load_offwords<DPT>(poffs + g * Dt);
 #pragma unroll
-    for (int g = 0; g < 4; ++g) {  // at most 16 channels = 4 groups per chunk
+    for (int g = 0; g < 4; ++g) {  // up to 4 groups (16 channels) at a time
         if (g < ng) {
             int o[DPT];
 #pragma unroll
@@ -643,6 +643,15 @@ __device__ __forceinline__ void sb_trials(Acc (&acc)[DPT][SPT], const Acc *Pl,
             }
         }
     }
+}
+
+// The trial loop over a chunk's ng groups (up to 8: 32 channels), four at a
+// time.
+template <typename Acc, int DPT, int SPT>
+__device__ __forceinline__ void sb_trials(Acc (&acc)[DPT][SPT], const Acc *Pl,
+                                          const uint16_t *poffs, int Dt, int ng) {
+    sb_trials4<Acc, DPT, SPT>(acc, Pl, poffs, Dt, min(ng, 4));
+    if (ng > 4) sb_trials4<Acc, DPT, SPT>(acc, Pl, poffs + 4 * Dt, Dt, ng - 4);
 }
 
 // kind 2: sub-band partial sums with a producer warp. Warps [0, NC) compute;

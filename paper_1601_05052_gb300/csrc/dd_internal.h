@@ -101,6 +101,10 @@ struct FwdTables {
     int2 *d_live = nullptr;
 };
 
+// Staging choices of the variant grid per (kernel key, CTA shape): 4 chunk
+// sizes by 3 pipeline depths, staging depth innermost (dd_variant_get).
+constexpr int kStagingChoices = 12;
+
 // Sub-band (kind 2) geometry: channels per group, distinct delay patterns a
 // group may have inside one DM tile.
 constexpr int kSbGroup = 4;

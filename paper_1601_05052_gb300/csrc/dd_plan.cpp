@@ -112,8 +112,9 @@ dd_status check_variant_shape(const dd_variant &v) {
         return fail(DD_ERR_ARG, "variant (kind, dm_per_thread, samples_per_thread) not compiled");
     if (v.warps_dm < 1 || v.warps_time < 1 || v.warps_dm * v.warps_time > max_trial_warps(v.kind))
         return fail(DD_ERR_ARG, "variant warps_dm * warps_time must be in [1, 8] (kind 4: [1, 16])");
-    if (v.chans_per_stage != 4 && v.chans_per_stage != 8 && v.chans_per_stage != 16)
-        return fail(DD_ERR_ARG, "variant chans_per_stage must be 4, 8 or 16");
+    if (v.chans_per_stage != 4 && v.chans_per_stage != 8 && v.chans_per_stage != 16 &&
+        v.chans_per_stage != 32)
+        return fail(DD_ERR_ARG, "variant chans_per_stage must be 4, 8, 16 or 32");
     if (v.stages < 2 || v.stages > 4) return fail(DD_ERR_ARG, "variant stages must be 2..4");
     return DD_OK;
 }
@@ -725,12 +726,12 @@ dd_status dd_plan_set_launch_order(dd_plan p, int32_t order) {
 // key with every CTA shape, then chunk size and staging depth innermost.
 namespace {
 const int kShapes[6][2] = {{4, 2}, {2, 4}, {8, 1}, {1, 8}, {4, 1}, {2, 2}};
-const int kCch[3] = {8, 16, 4};
+const int kCch[4] = {8, 16, 4, 32};
 const int kStages[3] = {3, 2, 4};
 }  // namespace
 
 int32_t dd_variant_count(void) {
-    return int32_t(fwd_compiled_keys().size()) * 6 * 3 * 3;
+    return int32_t(fwd_compiled_keys().size()) * 6 * kStagingChoices;
 }
 
 dd_status dd_variant_get(int32_t i, dd_variant *v) {
@@ -738,8 +739,8 @@ dd_status dd_variant_get(int32_t i, dd_variant *v) {
     const auto &keys = fwd_compiled_keys();
     const int st = i % 3;
     i /= 3;
-    const int cc = i % 3;
-    i /= 3;
+    const int cc = i % 4;
+    i /= 4;
     const int ws = i % 6;
     i /= 6;
     const FwdKernelKey k = keys[size_t(i)];

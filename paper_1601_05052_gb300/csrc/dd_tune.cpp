@@ -48,8 +48,9 @@ dd_status sweep_variants(int32_t budget_ms, double flop,
         return DD_OK;
     };
     const int n = dd_variant_count();
-    // pass 1: staging fixed at the first choice of the grid (index % 9 == 0)
-    for (int i = 0; i < n && !(over() && !tried.empty()); i += 9) {
+    // pass 1: staging fixed at the first choice of the grid (8 channels per
+    // stage, 3 stages)
+    for (int i = 0; i < n && !(over() && !tried.empty()); i += kStagingChoices) {
         dd_variant v;
         dd_variant_get(i, &v);
         dd_status s = run(v);

@@ -101,7 +101,7 @@ def test_variant_grid():
     for v in vs:
         assert v["warps_dm"] * v["warps_time"] <= (16 if v["kind"] == 4 else 8)
         assert v["kind"] in (0, 1, 2, 3, 4, 5) and (v["kind"] != 1 or v["samples_per_thread"] % 2 == 1)
-        assert v["chans_per_stage"] in (4, 8, 16) and 2 <= v["stages"] <= 4
+        assert v["chans_per_stage"] in (4, 8, 16, 32) and 2 <= v["stages"] <= 4
     # kind 4 covers DM tiles of 128 trials
     assert any(v["kind"] == 4 and v["dm_per_thread"] * v["warps_dm"] == 128 for v in vs)
 
