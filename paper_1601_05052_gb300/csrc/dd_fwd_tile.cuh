@@ -645,13 +645,20 @@ __device__ __forceinline__ void sb_trials4(Acc (&acc)[DPT][SPT], const Acc *Pl,
     }
 }
 
-// The trial loop over a chunk's ng groups (up to 8: 32 channels), four at a
-// time.
-template <typename Acc, int DPT, int SPT>
+// The trial loop over a chunk's ng groups: up to 4 (16 channels) with FP32
+// input, up to 8 (32 channels, four at a time) with 8- and 16-bit input,
+// whose staging bytes leave room for 32-channel chunks. (A second pass in
+// the FP32 kernels, even one never taken, measured 5.7 % slower at the
+// survey scale on GB300, so they have none.)
+template <typename T, typename Acc, int DPT, int SPT>
 __device__ __forceinline__ void sb_trials(Acc (&acc)[DPT][SPT], const Acc *Pl,
                                           const uint16_t *poffs, int Dt, int ng) {
-    sb_trials4<Acc, DPT, SPT>(acc, Pl, poffs, Dt, min(ng, 4));
-    if (ng > 4) sb_trials4<Acc, DPT, SPT>(acc, Pl, poffs + 4 * Dt, Dt, ng - 4);
+    if constexpr (sizeof(T) == 4) {
+        sb_trials4<Acc, DPT, SPT>(acc, Pl, poffs, Dt, ng);
+    } else {
+        sb_trials4<Acc, DPT, SPT>(acc, Pl, poffs, Dt, min(ng, 4));
+        if (ng > 4) sb_trials4<Acc, DPT, SPT>(acc, Pl, poffs + 4 * Dt, Dt, ng - 4);
+    }
 }
 
 // kind 2: sub-band partial sums with a producer warp. Warps [0, NC) compute;
@@ -753,7 +760,7 @@ __device__ __forceinline__ void fwd_tile_sb(const FwdArgs &a, int dtile, int tti
         compute_barrier(nc * 32);
         if (*gave_up) continue;  // no arrival: the producer's next wait fails too
         if (tid == 0) mbar_arrive(&empty[slot]);  // nothing reads this staging slot any more
-        sb_trials<Acc, DPT, SPT>(acc, P + lb, poffs + wd * DPT, a.Dt, ng);
+        sb_trials<T, Acc, DPT, SPT>(acc, P + lb, poffs + wd * DPT, a.Dt, ng);
     }
     kbase += uint32_t(n_chunks);
     if (!*gave_up) store_lane_strided<Acc, DPT, SPT>(a, acc, dtile, b, t0, wd, lb);
@@ -855,7 +862,7 @@ __device__ __forceinline__ void fwd_tile_ws(const FwdArgs &a, int dtile, int tti
         const uint16_t *poffs =
             reinterpret_cast<const uint16_t *>(pb + a.p_elems * int(sizeof(Acc))) + wd * DPT;
         const int ng = (min(a.cch, a.C - (kr.x + k) * a.cch) + kSbG - 1) / kSbG;
-        sb_trials<Acc, DPT, SPT>(acc, reinterpret_cast<const Acc *>(pb) + lb, poffs, a.Dt, ng);
+        sb_trials<T, Acc, DPT, SPT>(acc, reinterpret_cast<const Acc *>(pb) + lb, poffs, a.Dt, ng);
         __syncwarp();
         if (lane == 0) mbar_arrive(&empty_p[ps]);
     }

@@ -211,6 +211,8 @@ dd_status build_fwd_tables(dd_plan_s *p, const dd_variant &v, FwdTables *out) {
     if (int64_t(t.n_ttiles) * t.n_dtiles > 0x7fffffffLL)
         return fail(DD_ERR_ARG, "too many tiles for this variant");
     if (sb && t.Dt % 8 != 0) return fail(DD_ERR_ARG, "sub-band variants need 8 | DM tile");
+    if (sb && cch > 16 && p->dtype == DD_F32)
+        return fail(DD_ERR_ARG, "sub-band variants with FP32 input stage at most 16 channels");
 
     const int G_pad = t.C_pad / kSbGroup;
     // desc: each channel's union window {ws, len, soff} per DM tile (the
