@@ -75,6 +75,8 @@ def _args():
                          "of tuning (e.g. one a tuned run printed)")
     ap.add_argument("--dtype", choices=["f32", "f16", "bf16", "u8"], default=None,
                     help="with --only survey_precisions: that input type alone")
+    ap.add_argument("--launch-order", choices=["dm", "time"], default=None,
+                    help="with --only lofar: the tiles' launch order (default: the tuned one)")
     ap.add_argument("--n-out", type=int, default=None,
                     help="with --only lofar: output samples (default: the full 200000)")
     ap.add_argument("--tune-ms", type=int, default=0,
@@ -466,7 +468,7 @@ def _case_survey_precisions(torch, flush, n_rep, f32_ms=None,
     return out
 
 
-def _case_lofar(torch, n_rep, peaks, tune=True, variant=None, n_out=None):
+def _case_lofar(torch, n_rep, peaks, tune=True, variant=None, n_out=None, order=None):
     """The paper's LOFAR instance (Section IV): 32 channels of 0.195 MHz from
     138 MHz, 5 us sampling, 2048 trial DMs 0-511.75, 200000 samples (1 s),
     FP32, unit weights. One DM step moves the lowest channel by ~900
@@ -484,6 +486,8 @@ def _case_lofar(torch, n_rep, peaks, tune=True, variant=None, n_out=None):
         p.variant = variant
     elif tune:
         p.tune(budget_ms=8000)
+    if order:
+        p.launch_order = order
     x = _rand_input(torch, g, p, 13, "f32")
     w = torch.ones(p.n_chan, device="cuda")
     o = torch.empty(p.out_shape, device="cuda")
@@ -551,7 +555,8 @@ def run_only(args):
     elif args.only == "small_graph":
         out = _case_small_graph(torch, n, tune=tune)
     elif args.only == "lofar":
-        out = _case_lofar(torch, n, peaks, tune=tune, variant=variant, n_out=args.n_out)
+        out = _case_lofar(torch, n, peaks, tune=tune, variant=variant, n_out=args.n_out,
+                          order=args.launch_order)
     elif args.only == "survey_precisions":
         out = _case_survey_precisions(torch, flush, n,
                                       dtypes=(args.dtype,) if args.dtype else

@@ -540,3 +540,44 @@ def test_launch_orders_give_identical_results(dtype):
     assert _lib.load().dd_plan_set_launch_order(plan._h, 2) == 1  # DD_ERR_ARG
     assert plan.launch_order == "time"
     plan.check_device()
+
+
+@pytest.mark.parametrize("dtype", ["f32", "u8", "f16", "bf16"])
+def test_64ch_64dm_4096_tuned_full(dtype):
+    """The 64-channel workload and its 8/16-bit forms in the variant the
+    tuner picks for them (the benchmark replays that variant's launches from
+    a CUDA graph): the whole output against the oracle, before and after
+    tuning, also from inside a captured graph."""
+    name = "lband64" if dtype == "f32" else "lband64_" + dtype
+    s, sh, x, w = _setup_case(name, dtype, "ones" if dtype == "f32" else "uniform", 3)
+    plan = Plan.from_setup(s)
+    check_full(plan, x, w, sh, dtype, "default " + dtype)
+    plan.tune(budget_ms=2000)
+    check_full(plan, x, w, sh, dtype, "tuned %s %s" % (dtype, plan.variant))
+    xd, wd = to_dev(x, dtype), weights_dev(w, dtype)
+    out = torch.empty(plan.out_shape, dtype=plan.out_dtype, device="cuda")
+    plan.execute(xd, wd, out)
+    torch.cuda.synchronize()
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph):
+        for _ in range(3):
+            plan.execute(xd, wd, out)
+    out.zero_()
+    graph.replay()
+    torch.cuda.synchronize()
+    if dtype == "u8":
+        np.testing.assert_array_equal(out.cpu().numpy().astype(np.int64),
+                                      oracle.forward_u8(x, w, sh, s.n_out))
+    else:
+        ref, ab = oracle.forward(x, w, sh, s.n_out, dtype=dtype, with_absum=True)
+        assert_float_parity(out.cpu().numpy(), ref, ab, what="graph " + dtype)
+    # a variant change after the capture keeps the captured tables alive
+    plan.variant = dict(kind=0, dm_per_thread=4, samples_per_thread=4, warps_dm=4, warps_time=2,
+                        chans_per_stage=8, stages=3)
+    out.zero_()
+    graph.replay()
+    torch.cuda.synchronize()
+    if dtype == "u8":
+        np.testing.assert_array_equal(out.cpu().numpy().astype(np.int64),
+                                      oracle.forward_u8(x, w, sh, s.n_out))
+    plan.check_device()
