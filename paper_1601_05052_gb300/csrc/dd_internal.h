@@ -204,8 +204,11 @@ void cache_store(const std::string &key, const dd_variant &v, bool time_major);
 
 // Two-pass sweep of the variant grid (dd_tune.cpp). time_ms(v, &ms) sets ms
 // <= 0 for variants that do not fit; returns the fastest in *best.
+// between_passes (may be empty) sees pass 1's fastest variant before pass 2
+// starts (the plan tuner settles the launch order there).
 dd_status sweep_variants(int32_t budget_ms, double flop,
                          const std::function<dd_status(const dd_variant &, double *)> &time_ms,
-                         dd_variant *best, dd_tune_report *rep);
+                         dd_variant *best, dd_tune_report *rep,
+                         const std::function<dd_status(const dd_variant &)> &between_passes = {});
 
 }  // namespace dd
