@@ -581,3 +581,33 @@ def test_64ch_64dm_4096_tuned_full(dtype):
         np.testing.assert_array_equal(out.cpu().numpy().astype(np.int64),
                                       oracle.forward_u8(x, w, sh, s.n_out))
     plan.check_device()
+
+
+@pytest.mark.parametrize("name,variant", [
+    ("lband64_x96", dict(kind=5, dm_per_thread=4, samples_per_thread=8, warps_dm=8, warps_time=1,
+                         chans_per_stage=16, stages=3)),
+    ("lband64_4dm_x384", dict(kind=0, dm_per_thread=4, samples_per_thread=8, warps_dm=1,
+                              warps_time=8, chans_per_stage=4, stages=3)),
+])
+def test_many_beam_points_sampled(name, variant):
+    """The benchmark's 96-beam and HBM-bound 384-beam FP32 points (64
+    channels over 1400-1500 MHz) in the variants it times: 4000 sampled
+    outputs over all beams, plus the first and last beam's corners."""
+    s = synth.setup(name)
+    sh = oracle.shift_table(s.freqs(), s.f_ref, s.t_samp, s.dms())
+    x = synth.make_input(s, sh, seed=7, pulses=synth.pulse_plan(s, 7))
+    w = synth.make_weights(s.n_chan, 7, "uniform")
+    plan = Plan.from_setup(s)
+    plan.variant = variant
+    out = plan.execute(to_dev(x, "f32"), weights_dev(w, "f32"))
+    torch.cuda.synchronize()
+    rng = np.random.default_rng(25)
+    n = 4000
+    pb = np.concatenate([rng.integers(0, s.batch, n), [0, 0, s.batch - 1, s.batch - 1]])
+    pd = np.concatenate([rng.integers(0, s.n_dm, n), [0, s.n_dm - 1, 0, s.n_dm - 1]])
+    pt = np.concatenate([rng.integers(0, s.n_out, n), [0, s.n_out - 1, s.n_out - 1, 0]])
+    got = out[torch.from_numpy(pb).cuda(), torch.from_numpy(pd).cuda(),
+              torch.from_numpy(pt).cuda()].cpu().numpy()
+    ref, ab = oracle.forward_points(x, w, sh, pb, pd, pt)
+    assert_float_parity(got, ref, ab, what="%s %s" % (name, variant))
+    plan.check_device()
