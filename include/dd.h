@@ -83,10 +83,12 @@ typedef struct dd_stream_s *dd_stream;
  * kind 4: kind 2 in CTAs of up to 16 trial warps (one CTA per SM).
  * kind 5: kind 0 that reuses the loaded operands for a trial whose delay in
  *         the channel equals the previous trial's.
+ * kind 6: kind 4 with one partial-sum slot and a second barrier per chunk,
+ *         so that FP32 input fits chunks of 32 channels.
  * Results do not depend on the variant beyond FP32 summation order (8-bit
  * input: bit-identical). */
 typedef struct {
-    int32_t kind;                /* 0..5, see above                         */
+    int32_t kind;                /* 0..6, see above                         */
     int32_t dm_per_thread;       /* DMs accumulated per thread (registers) */
     int32_t samples_per_thread;  /* samples accumulated per thread          */
     int32_t warps_dm;            /* warps along the DM axis of a CTA        */

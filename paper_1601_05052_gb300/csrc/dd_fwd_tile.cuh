@@ -39,6 +39,9 @@
 //  kind 5, lane-strided with shared delays: kind 0, but a trial whose delay
 //    in the channel equals the previous trial's reuses the operands already
 //    in registers.
+//  kind 6, one-slot wide sub-band: kind 4 with a single partial-sum slot
+//    (one more barrier per chunk) and up to 8 groups per chunk, so that
+//    FP32 input fits 32-channel chunks.
 #pragma once
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
@@ -55,7 +58,7 @@
 #define DD_FWD_KEYS(X)                                                                    \
     X(0, 2, 4) X(0, 4, 2) X(0, 4, 4) X(0, 8, 2) X(0, 8, 4) X(0, 4, 8) X(1, 8, 9) X(2, 4, 4) \
         X(2, 4, 8) X(2, 8, 4) X(2, 8, 2) X(3, 8, 4) X(3, 4, 8) X(3, 8, 2) X(4, 8, 4) X(4, 4, 8) \
-            X(5, 4, 8) X(5, 8, 4)
+            X(5, 4, 8) X(5, 8, 4) X(6, 4, 8)
 
 namespace dd {
 
@@ -400,7 +403,7 @@ template <int KIND>
 __device__ __forceinline__ void fwd_init_barriers(uint64_t *bars, int stages) {
     if (threadIdx.x == 0) {
         const int n_warps = int(blockDim.x >> 5);
-        const int releasers = KIND == 3 ? kWsBuilders : ((KIND == 2 || KIND == 4) ? 1 : n_warps);
+        const int releasers = KIND == 3 ? kWsBuilders : (is_subband(KIND) ? 1 : n_warps);
         for (int s = 0; s < stages; ++s) {
             mbar_init(&bars[s], 1);
             mbar_init(&bars[8 + s], uint32_t(releasers));
@@ -645,15 +648,15 @@ __device__ __forceinline__ void sb_trials4(Acc (&acc)[DPT][SPT], const Acc *Pl,
     }
 }
 
-// The trial loop over a chunk's ng groups: up to 4 (16 channels) with FP32
-// input, up to 8 (32 channels, four at a time) with 8- and 16-bit input,
-// whose staging bytes leave room for 32-channel chunks. (A second pass in
-// the FP32 kernels, even one never taken, measured 5.7 % slower at the
-// survey scale on GB300, so they have none.)
-template <typename T, typename Acc, int DPT, int SPT>
+// The trial loop over a chunk's ng groups: up to 4 (16 channels), or with G8
+// up to 8 (32 channels, four at a time): 8- and 16-bit input, whose staging
+// bytes leave room for 32-channel chunks, and kind 6. (A second pass in the
+// FP32 kinds 2-4, even one never taken, measured 5.7 % slower at the survey
+// scale on GB300, so they have none.)
+template <bool G8, typename Acc, int DPT, int SPT>
 __device__ __forceinline__ void sb_trials(Acc (&acc)[DPT][SPT], const Acc *Pl,
                                           const uint16_t *poffs, int Dt, int ng) {
-    if constexpr (sizeof(T) == 4) {
+    if constexpr (!G8) {
         sb_trials4<Acc, DPT, SPT>(acc, Pl, poffs, Dt, ng);
     } else {
         sb_trials4<Acc, DPT, SPT>(acc, Pl, poffs, Dt, min(ng, 4));
@@ -671,7 +674,10 @@ __device__ __forceinline__ void sb_trials(Acc (&acc)[DPT][SPT], const Acc *Pl,
 // never overwrites what slower warps still read. (Replacing the barrier by
 // per-warp mbarrier hand-offs, so that a warp builds chunk k+1 before its
 // trials on chunk k, measured slower on GB300.)
-template <typename T, int DPT, int SPT, bool LIVE>
+// ONE_SLOT (kind 6): a single partial-sum slot, so that FP32 input fits
+// 32-channel chunks; a second barrier per chunk then keeps the next build
+// from overwriting series that slower warps still read.
+template <typename T, int DPT, int SPT, bool LIVE, bool ONE_SLOT = false>
 __device__ __forceinline__ void fwd_tile_sb(const FwdArgs &a, int dtile, int ttile, int b,
                                             uint64_t *bars, unsigned char *stage0,
                                             uint32_t &kbase) {
@@ -745,7 +751,7 @@ __device__ __forceinline__ void fwd_tile_sb(const FwdArgs &a, int dtile, int tti
         const T *raw = reinterpret_cast<const T *>(sb);
         const int4 *bd = reinterpret_cast<const int4 *>(sb + a.stage_data_bytes + poffs_bytes);
         const Wt *sw = reinterpret_cast<const Wt *>(sb + a.stage_data_bytes + st.tab_bytes);
-        unsigned char *pb = pslot0 + (kg & 1u) * pslot_bytes;
+        unsigned char *pb = pslot0 + (ONE_SLOT ? 0u : (kg & 1u)) * pslot_bytes;
         Acc *P = reinterpret_cast<Acc *>(pb);
         uint16_t *poffs = reinterpret_cast<uint16_t *>(pb + a.p_elems * int(sizeof(Acc)));
         const int ng = (min(a.cch, a.C - (kr.x + k) * a.cch) + kSbG - 1) / kSbG;
@@ -758,9 +764,19 @@ __device__ __forceinline__ void fwd_tile_sb(const FwdArgs &a, int dtile, int tti
             for (int i = tid; i < int(poffs_bytes / 4); i += nc * 32) dst[i] = src[i];
         }
         compute_barrier(nc * 32);
-        if (*gave_up) continue;  // no arrival: the producer's next wait fails too
-        if (tid == 0) mbar_arrive(&empty[slot]);  // nothing reads this staging slot any more
-        sb_trials<T, Acc, DPT, SPT>(acc, P + lb, poffs + wd * DPT, a.Dt, ng);
+        if constexpr (ONE_SLOT) {
+            // every warp reaches both barriers of a chunk, whatever the flag
+            // (the producer may set it between two warps' reads)
+            if (!*gave_up) {
+                if (tid == 0) mbar_arrive(&empty[slot]);
+                sb_trials<true, Acc, DPT, SPT>(acc, P + lb, poffs + wd * DPT, a.Dt, ng);
+            }
+            compute_barrier(nc * 32);
+        } else {
+            if (*gave_up) continue;  // no arrival: the producer's next wait fails too
+            if (tid == 0) mbar_arrive(&empty[slot]);  // nothing reads this staging slot any more
+            sb_trials<(sizeof(T) < 4), Acc, DPT, SPT>(acc, P + lb, poffs + wd * DPT, a.Dt, ng);
+        }
     }
     kbase += uint32_t(n_chunks);
     if (!*gave_up) store_lane_strided<Acc, DPT, SPT>(a, acc, dtile, b, t0, wd, lb);
@@ -862,7 +878,8 @@ __device__ __forceinline__ void fwd_tile_ws(const FwdArgs &a, int dtile, int tti
         const uint16_t *poffs =
             reinterpret_cast<const uint16_t *>(pb + a.p_elems * int(sizeof(Acc))) + wd * DPT;
         const int ng = (min(a.cch, a.C - (kr.x + k) * a.cch) + kSbG - 1) / kSbG;
-        sb_trials<T, Acc, DPT, SPT>(acc, reinterpret_cast<const Acc *>(pb) + lb, poffs, a.Dt, ng);
+        sb_trials<(sizeof(T) < 4), Acc, DPT, SPT>(acc, reinterpret_cast<const Acc *>(pb) + lb,
+                                                  poffs, a.Dt, ng);
         __syncwarp();
         if (lane == 0) mbar_arrive(&empty_p[ps]);
     }
@@ -877,6 +894,8 @@ __device__ __forceinline__ void fwd_tile_any(const FwdArgs &a, int dtile, int tt
                                              uint32_t &kbase) {
     if constexpr (KIND == 2 || KIND == 4)
         fwd_tile_sb<T, DPT, SPT, LIVE>(a, dtile, ttile, b, bars, stage0, kbase);
+    else if constexpr (KIND == 6)
+        fwd_tile_sb<T, DPT, SPT, LIVE, true>(a, dtile, ttile, b, bars, stage0, kbase);
     else if constexpr (KIND == 3)
         fwd_tile_ws<T, DPT, SPT, LIVE>(a, dtile, ttile, b, bars, stage0, kbase);
     else

@@ -5,7 +5,9 @@
 // kind 1: register windows; kind 2: sub-band partial series (groups of four
 // channels) with a producer warp; kind 3: kind 2 with warp-specialised
 // builders; kind 4: kind 2 in CTAs of up to 16 trial warps; kind 5: kind 0
-// with operand reuse between trials that share a channel's delay.
+// with operand reuse between trials that share a channel's delay; kind 6:
+// kind 4 with one partial-sum slot and up to 8 groups per chunk, which lets
+// FP32 input stage 32 channels at a time.
 #pragma once
 
 #include <cuda_runtime.h>
@@ -17,14 +19,16 @@ constexpr int kWsBuilders = 4;
 
 // Warps a CTA has beyond its warps_dm * warps_time trial warps.
 __host__ __device__ constexpr int extra_warps(int kind) {
-    return kind == 3 ? kWsBuilders : ((kind == 2 || kind == 4) ? 1 : 0);
+    return kind == 3 ? kWsBuilders : ((kind == 2 || kind == 4 || kind == 6) ? 1 : 0);
 }
 // Sub-band kinds (partial series per channel group).
 __host__ __device__ constexpr bool is_subband(int kind) {
-    return kind == 2 || kind == 3 || kind == 4;
+    return kind == 2 || kind == 3 || kind == 4 || kind == 6;
 }
 // Largest trial-warp count of a CTA.
-__host__ __device__ constexpr int max_trial_warps(int kind) { return kind == 4 ? 16 : 8; }
+__host__ __device__ constexpr int max_trial_warps(int kind) {
+    return (kind == 4 || kind == 6) ? 16 : 8;
+}
 // Launch bounds of the forward kernels: threads per CTA and resident CTAs
 // per SM that the register allocation must allow.
 __host__ __device__ constexpr int fwd_max_threads(int kind) {

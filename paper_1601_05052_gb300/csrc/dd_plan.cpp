@@ -111,7 +111,8 @@ dd_status check_variant_shape(const dd_variant &v) {
     if (!fwd_variant_compiled(v.kind, v.dm_per_thread, v.samples_per_thread))
         return fail(DD_ERR_ARG, "variant (kind, dm_per_thread, samples_per_thread) not compiled");
     if (v.warps_dm < 1 || v.warps_time < 1 || v.warps_dm * v.warps_time > max_trial_warps(v.kind))
-        return fail(DD_ERR_ARG, "variant warps_dm * warps_time must be in [1, 8] (kind 4: [1, 16])");
+        return fail(DD_ERR_ARG,
+                    "variant warps_dm * warps_time must be in [1, 8] (kinds 4 and 6: [1, 16])");
     if (v.chans_per_stage != 4 && v.chans_per_stage != 8 && v.chans_per_stage != 16 &&
         v.chans_per_stage != 32)
         return fail(DD_ERR_ARG, "variant chans_per_stage must be 4, 8, 16 or 32");
@@ -211,8 +212,8 @@ dd_status build_fwd_tables(dd_plan_s *p, const dd_variant &v, FwdTables *out) {
     if (int64_t(t.n_ttiles) * t.n_dtiles > 0x7fffffffLL)
         return fail(DD_ERR_ARG, "too many tiles for this variant");
     if (sb && t.Dt % 8 != 0) return fail(DD_ERR_ARG, "sub-band variants need 8 | DM tile");
-    if (sb && cch > 16 && p->dtype == DD_F32)
-        return fail(DD_ERR_ARG, "sub-band variants with FP32 input stage at most 16 channels");
+    if (sb && v.kind != 6 && cch > 16 && p->dtype == DD_F32)
+        return fail(DD_ERR_ARG, "sub-band kinds 2-4 with FP32 input stage at most 16 channels");
 
     const int G_pad = t.C_pad / kSbGroup;
     // desc: each channel's union window {ws, len, soff} per DM tile (the
@@ -381,6 +382,8 @@ dd_status build_fwd_tables(dd_plan_s *p, const dd_variant &v, FwdTables *out) {
     size_t p_bytes = 0;
     if (v.kind == 2 || v.kind == 4)  // 2 partial-sum slots, each with the chunk's trial offsets
         p_bytes = size_t(2) * (size_t(t.p_elems) * 4 + size_t(cch / kSbGroup) * t.Dt * 2);
+    if (v.kind == 6)  // 1 partial-sum slot
+        p_bytes = size_t(t.p_elems) * 4 + size_t(cch / kSbGroup) * t.Dt * 2;
     if (v.kind == 3)  // 3 partial-sum slots, each with the chunk's trial offsets
         p_bytes = size_t(3) * (size_t(t.p_elems) * 4 + size_t(cch / kSbGroup) * t.Dt * 2);
     t.smem_bytes = 128 + size_t(v.stages) * (t.stage_data_bytes + t.stage_offs_bytes) + p_bytes;
@@ -756,7 +759,7 @@ dd_status dd_variant_get(int32_t i, dd_variant *v) {
     i /= 6;
     const FwdKernelKey k = keys[size_t(i)];
     // kind 4 runs twice the trial warps of each shape along DM
-    const int wdm = kShapes[ws][0] * (k.kind == 4 ? 2 : 1);
+    const int wdm = kShapes[ws][0] * ((k.kind == 4 || k.kind == 6) ? 2 : 1);
     *v = dd_variant{k.kind, k.dpt, k.spt, wdm, kShapes[ws][1], kCch[cc], kStages[st]};
     return DD_OK;
 }

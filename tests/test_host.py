@@ -99,8 +99,8 @@ def test_variant_grid():
     keys = {(v["kind"], v["dm_per_thread"], v["samples_per_thread"]) for v in vs}
     assert (0, 4, 4) in keys and (1, 8, 9) in keys and (2, 4, 8) in keys and (4, 8, 4) in keys
     for v in vs:
-        assert v["warps_dm"] * v["warps_time"] <= (16 if v["kind"] == 4 else 8)
-        assert v["kind"] in (0, 1, 2, 3, 4, 5) and (v["kind"] != 1 or v["samples_per_thread"] % 2 == 1)
+        assert v["warps_dm"] * v["warps_time"] <= (16 if v["kind"] in (4, 6) else 8)
+        assert v["kind"] in (0, 1, 2, 3, 4, 5, 6) and (v["kind"] != 1 or v["samples_per_thread"] % 2 == 1)
         assert v["chans_per_stage"] in (4, 8, 16, 32) and 2 <= v["stages"] <= 4
     # kind 4 covers DM tiles of 128 trials
     assert any(v["kind"] == 4 and v["dm_per_thread"] * v["warps_dm"] == 128 for v in vs)
