@@ -648,20 +648,33 @@ __device__ __forceinline__ void sb_trials4(Acc (&acc)[DPT][SPT], const Acc *Pl,
     }
 }
 
-// The trial loop over a chunk's ng groups: up to 4 (16 channels), or with G8
-// up to 8 (32 channels, four at a time): 8- and 16-bit input, whose staging
-// bytes leave room for 32-channel chunks, and kind 6. (A second pass in the
-// FP32 kinds 2-4, even one never taken, measured 5.7 % slower at the survey
-// scale on GB300, so they have none.)
-template <bool G8, typename Acc, int DPT, int SPT>
+// The trial loop over a chunk's ng groups, four at a time. PASSES: 1 = at
+// most 4 groups (16 channels); 2 = up to 8 (32 channels) as two inlined
+// passes; 0 = up to 8 as a loop over one copy of the pass. Which form is
+// fastest depends on the kernel (GB300, survey scale): the FP32 kinds 2-4
+// keep one pass (a second one, even never taken, cost 5.7 %); 8-bit input
+// takes two inlined passes (2.26 against 2.32 ms as a loop); 16-bit input
+// and kind 6 take the loop (16-bit kind 4: 2.37 against 2.44 ms; FP32 kind
+// 6: 2.34 against 2.55 ms, where the inlined form spills).
+template <int PASSES, typename Acc, int DPT, int SPT>
 __device__ __forceinline__ void sb_trials(Acc (&acc)[DPT][SPT], const Acc *Pl,
                                           const uint16_t *poffs, int Dt, int ng) {
-    if constexpr (!G8) {
+    if constexpr (PASSES == 1) {
         sb_trials4<Acc, DPT, SPT>(acc, Pl, poffs, Dt, ng);
-    } else {
+    } else if constexpr (PASSES == 2) {
         sb_trials4<Acc, DPT, SPT>(acc, Pl, poffs, Dt, min(ng, 4));
         if (ng > 4) sb_trials4<Acc, DPT, SPT>(acc, Pl, poffs + 4 * Dt, Dt, ng - 4);
+    } else {
+#pragma unroll 1
+        for (int g0 = 0; g0 < ng; g0 += 4)
+            sb_trials4<Acc, DPT, SPT>(acc, Pl, poffs + g0 * Dt, Dt, min(ng - g0, 4));
     }
+}
+
+// The trial-loop form of a sub-band kernel (see sb_trials).
+template <typename T, bool ONE_SLOT>
+__host__ __device__ constexpr int sb_passes() {
+    return sizeof(T) == 1 ? 2 : ((ONE_SLOT || sizeof(T) == 2) ? 0 : 1);
 }
 
 // kind 2: sub-band partial sums with a producer warp. Warps [0, NC) compute;
@@ -769,13 +782,15 @@ __device__ __forceinline__ void fwd_tile_sb(const FwdArgs &a, int dtile, int tti
             // (the producer may set it between two warps' reads)
             if (!*gave_up) {
                 if (tid == 0) mbar_arrive(&empty[slot]);
-                sb_trials<true, Acc, DPT, SPT>(acc, P + lb, poffs + wd * DPT, a.Dt, ng);
+                sb_trials<sb_passes<T, true>(), Acc, DPT, SPT>(acc, P + lb, poffs + wd * DPT, a.Dt,
+                                                               ng);
             }
             compute_barrier(nc * 32);
         } else {
             if (*gave_up) continue;  // no arrival: the producer's next wait fails too
             if (tid == 0) mbar_arrive(&empty[slot]);  // nothing reads this staging slot any more
-            sb_trials<(sizeof(T) < 4), Acc, DPT, SPT>(acc, P + lb, poffs + wd * DPT, a.Dt, ng);
+            sb_trials<sb_passes<T, false>(), Acc, DPT, SPT>(acc, P + lb, poffs + wd * DPT, a.Dt,
+                                                            ng);
         }
     }
     kbase += uint32_t(n_chunks);
@@ -878,8 +893,8 @@ __device__ __forceinline__ void fwd_tile_ws(const FwdArgs &a, int dtile, int tti
         const uint16_t *poffs =
             reinterpret_cast<const uint16_t *>(pb + a.p_elems * int(sizeof(Acc))) + wd * DPT;
         const int ng = (min(a.cch, a.C - (kr.x + k) * a.cch) + kSbG - 1) / kSbG;
-        sb_trials<(sizeof(T) < 4), Acc, DPT, SPT>(acc, reinterpret_cast<const Acc *>(pb) + lb,
-                                                  poffs, a.Dt, ng);
+        sb_trials<sb_passes<T, false>(), Acc, DPT, SPT>(
+            acc, reinterpret_cast<const Acc *>(pb) + lb, poffs, a.Dt, ng);
         __syncwarp();
         if (lane == 0) mbar_arrive(&empty_p[ps]);
     }

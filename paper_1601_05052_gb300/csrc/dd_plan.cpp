@@ -458,13 +458,14 @@ namespace {
 
 // Candidate default variants, best first; the first that fits the plan is
 // used until dd_tune or dd_plan_set_variant picks another.
-// (Measured on GB300: the wide sub-band kind with 64-trial by 256-sample
-// tiles and 16 channels per stage leads on the Apertif-like and 512-channel
-// setups, then kind 2's 64 x 128 tiles; the lane-strided kind 0 takes setups
-// whose delay patterns are too varied for sub-bands, e.g. wide
-// low-frequency bands.)
+// (Measured on GB300: the wide sub-band kinds with 64-trial by 256-sample
+// tiles lead on the Apertif-like and 512-channel setups, kind 6 with 32
+// channels per stage first (2.34 against 2.43 ms for kind 4 with 16 at the
+// survey scale), then kind 2's 64 x 128 tiles; the lane-strided kind 0
+// takes setups whose delay patterns are too varied for sub-bands, e.g.
+// wide low-frequency bands.)
 const dd_variant kDefaults[] = {
-    {4, 4, 8, 16, 1, 16, 2}, {2, 8, 4, 8, 1, 16, 2}, {2, 8, 4, 4, 2, 8, 2},
+    {6, 4, 8, 16, 1, 32, 2}, {4, 4, 8, 16, 1, 16, 2}, {2, 8, 4, 8, 1, 16, 2}, {2, 8, 4, 4, 2, 8, 2},
     {0, 4, 8, 4, 1, 8, 3},   {0, 4, 4, 4, 2, 8, 3},  {0, 4, 4, 4, 2, 4, 2},
     {0, 2, 4, 4, 2, 4, 2},   {0, 4, 2, 4, 1, 4, 2},
 };
