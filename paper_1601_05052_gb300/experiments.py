@@ -21,7 +21,11 @@ maximises the sum of GFLOP/s over all instances, and the speedup of the tuned
 optimum over it for each instance.
 
 Here a configuration is a compiled kernel variant (kind, DMs and samples per
-thread, warps along DM and time) at 16 channels per stage and 2 stages; the
+thread, warps along DM and time) at a fixed staging per setup: Apertif 16
+channels per stage, LOFAR 4 (a LOFAR DM step moves the lowest channel by ~900
+samples, so each trial of a tile stages its own window per channel, and a
+chunk holds at most 32 windows), 2 stages, with the launch order of the
+setup's tiles (LOFAR: time tiles fastest, which keeps its rows in L2); the
 variants that do not fit an instance are not meaningful for it. Inputs are
 seeded N(0,1) noise (performance does not depend on the values).
 
@@ -40,10 +44,10 @@ from . import Plan, variants
 SETUPS = {
     # Section IV: 20 000 samples/s, 1024 channels of 0.29 MHz from 1420 MHz
     "apertif": dict(n_chan=1024, f_lo=1420.0, chan_width=300.0 / 1024, t_samp=1 / 20000,
-                    n_out=20000),
+                    n_out=20000, chans_per_stage=16, order="dm"),
     # Section IV: 200 000 samples/s, 32 channels of ~0.19 MHz from 138 MHz
     "lofar": dict(n_chan=32, f_lo=138.0, chan_width=0.1953125, t_samp=1 / 200000,
-                  n_out=200000),
+                  n_out=200000, chans_per_stage=4, order="time"),
 }
 DDM = 0.25
 
@@ -55,8 +59,9 @@ def _plan(name, n_dm, dm0_only):
     return Plan(freqs, freqs[-1], s["t_samp"], dms, s["n_out"], batch=1)
 
 
-def _configs():
-    return [v for v in variants() if v["chans_per_stage"] == 16 and v["stages"] == 2]
+def _configs(name):
+    cch = SETUPS[name]["chans_per_stage"]
+    return [v for v in variants() if v["chans_per_stage"] == cch and v["stages"] == 2]
 
 
 def _time_ms(plan, x, w, o, reps=3):
@@ -76,7 +81,7 @@ def _time_ms(plan, x, w, o, reps=3):
 
 def run(name, dm0_only=False, instances=None, log=sys.stderr):
     instances = instances or [2 ** k for k in range(1, 13)]
-    configs = _configs()
+    configs = _configs(name)
     key = lambda v: tuple(v.values())
     table = {}  # instance -> {config key: GFLOP/s}
     rows = []
@@ -94,6 +99,7 @@ def run(name, dm0_only=False, instances=None, log=sys.stderr):
                 plan.variant = v
             except Exception:
                 continue  # not meaningful for this instance
+            plan.launch_order = SETUPS[name]["order"]
             perf[key(v)] = flop / (_time_ms(plan, x, w, o) * 1e6)
         table[n_dm] = perf
         vals = list(perf.values())
