@@ -39,23 +39,34 @@ dd_status sweep_variants(int32_t budget_ms, double flop,
                a.warps_time == b.warps_time && a.chans_per_stage == b.chans_per_stage &&
                a.stages == b.stages;
     };
-    auto run = [&](const dd_variant &v) -> dd_status {
+    // times v (once); *fits says whether it fitted the plan
+    auto run = [&](const dd_variant &v, bool *fits = nullptr) -> dd_status {
         for (auto &t : tried)
-            if (same(t.second, v)) return DD_OK;
+            if (same(t.second, v)) {
+                if (fits) *fits = true;
+                return DD_OK;
+            }
         double ms = -1.0;
         dd_status s = time_ms(v, &ms);
         if (s != DD_OK) return s;
         if (ms > 0) tried.emplace_back(ms, v);
+        if (fits) *fits = ms > 0;
         return DD_OK;
     };
     const int n = dd_variant_count();
-    // pass 1: staging fixed at the first choice of the grid (8 channels per
-    // stage, 3 stages)
+    // pass 1: every (kernel key, CTA shape) at the first staging choice of
+    // the grid that fits the plan (8 channels per stage and 3 stages first;
+    // a shape whose windows need smaller chunks, e.g. one staging a window
+    // per trial, gets the first smaller staging that fits)
     for (int i = 0; i < n && !(over() && !tried.empty()); i += kStagingChoices) {
-        dd_variant v;
-        dd_variant_get(i, &v);
-        dd_status s = run(v);
-        if (s != DD_OK) return s;
+        for (int j = 0; j < kStagingChoices; ++j) {
+            dd_variant v;
+            dd_variant_get(i + j, &v);
+            bool fits = false;
+            dd_status s = run(v, &fits);
+            if (s != DD_OK) return s;
+            if (fits) break;
+        }
     }
     // pass 2: every staging choice of the three best shapes
     std::vector<std::pair<double, dd_variant>> top = tried;

@@ -24,7 +24,8 @@ Here a configuration is a compiled kernel variant (kind, DMs and samples per
 thread, warps along DM and time) at a fixed staging per setup: Apertif 16
 channels per stage, LOFAR 4 (a LOFAR DM step moves the lowest channel by ~900
 samples, so each trial of a tile stages its own window per channel, and a
-chunk holds at most 32 windows), 2 stages, with the launch order of the
+chunk holds at most 32 windows; with every DM 0, 16 as for Apertif), 2
+stages, with the launch order of the
 setup's tiles (LOFAR: time tiles fastest, which keeps its rows in L2); the
 variants that do not fit an instance are not meaningful for it. Inputs are
 seeded N(0,1) noise (performance does not depend on the values).
@@ -59,8 +60,8 @@ def _plan(name, n_dm, dm0_only):
     return Plan(freqs, freqs[-1], s["t_samp"], dms, s["n_out"], batch=1)
 
 
-def _configs(name):
-    cch = SETUPS[name]["chans_per_stage"]
+def _configs(name, dm0_only=False):
+    cch = 16 if dm0_only else SETUPS[name]["chans_per_stage"]
     return [v for v in variants() if v["chans_per_stage"] == cch and v["stages"] == 2]
 
 
@@ -81,7 +82,7 @@ def _time_ms(plan, x, w, o, reps=3):
 
 def run(name, dm0_only=False, instances=None, log=sys.stderr):
     instances = instances or [2 ** k for k in range(1, 13)]
-    configs = _configs(name)
+    configs = _configs(name, dm0_only)
     key = lambda v: tuple(v.values())
     table = {}  # instance -> {config key: GFLOP/s}
     rows = []
