@@ -227,7 +227,10 @@ dd_status dd_grad_w_noalloc(dd_plan plan, const float *d_gout, const float *d_in
 /* ---- Auto-tuning (Section IV-A / V-A) ------------------------------------
  * Times every compiled variant that fits this plan on scratch buffers it
  * allocates and frees itself, keeps the fastest as the plan's variant and
- * fills *rep (nullable). budget_ms bounds the sweep (0 = no bound).
+ * fills *rep (nullable). budget_ms bounds the sweep (0 = no bound). Plans
+ * whose input and output exceed 16 MB are timed with L2 flushed before each
+ * timed launch; smaller ones warm (replayed back to back, their data stays
+ * in L2).
  * Tuning cache: when the environment variable DD_TUNE_CACHE names a file,
  * dd_tune appends one text line "<key> kind dpt spt warps_dm warps_time
  * chans_per_stage stages order" for the winner (order: its launch order, see
