@@ -58,7 +58,7 @@
 #define DD_FWD_KEYS(X)                                                                    \
     X(0, 2, 4) X(0, 4, 2) X(0, 4, 4) X(0, 8, 2) X(0, 8, 4) X(0, 4, 8) X(1, 8, 9) X(2, 4, 4) \
         X(2, 4, 8) X(2, 8, 4) X(2, 8, 2) X(3, 8, 4) X(3, 4, 8) X(3, 8, 2) X(4, 8, 4) X(4, 4, 8) \
-            X(5, 4, 8) X(5, 8, 4) X(6, 4, 8)
+            X(5, 4, 8) X(5, 8, 4) X(6, 4, 8) X(0, 4, 16)
 
 namespace dd {
 
