@@ -157,7 +157,7 @@ def test_subband_kinds_every_shape(dtype):
         ref, ab = oracle.forward(x, w, sh, S, dtype=dtype, with_absum=True)
     ran = {}
     for v in variants():
-        if v["kind"] not in (2, 3, 4) or v["stages"] == 4:
+        if v["kind"] not in (2, 3, 4, 6) or v["stages"] == 4:
             continue
         try:
             plan.variant = v
@@ -169,7 +169,43 @@ def test_subband_kinds_every_shape(dtype):
         else:
             assert_float_parity(out, ref, ab, what=str(v))
         ran[v["kind"]] = ran.get(v["kind"], 0) + 1
-    assert all(ran.get(k, 0) >= 3 for k in (2, 3, 4)), ran
+    assert all(ran.get(k, 0) >= 3 for k in (2, 3, 4)) and ran.get(6, 0) >= 1, ran
+    plan.check_device()
+
+
+def test_subband_u8_wide_integer_weights():
+    """8-bit sub-band kernels with integer weights far from the Q8 range:
+    random 16-bit values, both ends of the 16-bit range, zeros, and weights
+    beyond it (up to 2^20, negative too), with sums that still fit INT32;
+    every sub-band kind must stay bit-exact."""
+    from paper_1601_05052_gb300 import compute_shifts
+    C, D, S = 102, 300, 1100
+    freqs = 1420.0 + np.arange(C) * (300.0 / 1024)
+    sh = compute_shifts(freqs, freqs[-1], 50e-6, np.arange(D) * 0.25).astype(np.int64)
+    rng = np.random.default_rng(79)
+    t_in = S + int(sh.max())
+    stride = synth.padded_stride(t_in, "u8")
+    x = rng.integers(0, 256, size=(2, C, stride)).astype(np.uint8)
+    w = rng.integers(-32768, 32768, size=C).astype(np.int32)
+    w[[0, 5, 10]] = [-32768, 32767, 0]
+    w[[17, 42, 64, 101]] = [40000, -40000, 1 << 20, -32769]
+    w[rng.random(C) < 0.05] = 0
+    plan = Plan(shifts=sh, n_out=S, batch=2, dtype="u8")
+    xd, wd = to_dev(x, "u8"), weights_dev(w, "u8")
+    ref = oracle.forward_u8(x, w, sh, S)
+    assert np.abs(ref).max() < 2**31
+    ran = {}
+    for v in variants():
+        if v["kind"] not in (2, 3, 4, 6) or v["stages"] == 4:
+            continue
+        try:
+            plan.variant = v
+        except Exception:
+            continue
+        out = plan.execute(xd, wd).cpu().numpy()
+        np.testing.assert_array_equal(out.astype(np.int64), ref, err_msg=str(v))
+        ran[v["kind"]] = ran.get(v["kind"], 0) + 1
+    assert all(ran.get(k, 0) >= 1 for k in (2, 3, 4, 6)), ran
     plan.check_device()
 
 
