@@ -43,6 +43,9 @@ struct LaunchTracker {
     void destroy();
 };
 
+// Input segments of dd_execute_host's copy/compute pipeline.
+constexpr int kHostSegments = 8;
+
 // Per-variant staging tables of the forward kernel.
 //
 // The DM axis is cut into tiles of Dt trials, the time axis into tiles of Ts
@@ -64,9 +67,6 @@ struct LaunchTracker {
 //                     a variant whose chunks need more windows does not fit)
 //   offs[k][c][i] = smem element offset of sample t0 of trial k*Dt + i
 //                   in channel c (= smem_off + shift - win_start of its window)
-// Input segments of dd_execute_host's copy/compute pipeline.
-constexpr int kHostSegments = 8;
-
 struct FwdTables {
     dd_variant v{};
     int Dt = 0, Ts = 0;
@@ -84,9 +84,9 @@ struct FwdTables {
     uint16_t *d_offs = nullptr;
     // sub-band kinds only: d_offs holds per-group trial offsets into the
     // partial-sum buffer, [n_dtiles][C_pad/4][Dt]; d_bdesc the build blocks
-    // of every chunk, [n_dtiles][n_chunks][n_blocks] int4 (one block = 32
-    // consecutive partial-series elements, see build_fwd_tables); p_elems the
-    // partial-sum buffer length of one chunk.
+    // of every chunk, [n_dtiles][n_chunks][n_blocks] int4 (one block = up to
+    // 4 x 32 consecutive elements of one partial series, see
+    // build_fwd_tables); p_elems the partial-sum buffer length of one chunk.
     int4 *d_bdesc = nullptr;
     int n_blocks = 0;
     int p_elems = 0;
