@@ -367,6 +367,13 @@ def test_survey_scale_f32_sampled():
     for (_, d, t0, a) in pulses:
         col = out[0, :, t0].cpu().numpy()
         assert col[d] > 0.5 * a * s.n_chan
+    # the end-to-end path the benchmark's e2e times (pinned host buffers,
+    # segmented pulls and launches) gives the device path's array exactly
+    hx = torch.from_numpy(x).pin_memory()
+    hw = torch.from_numpy(w).pin_memory()
+    hout = torch.empty(plan.out_shape, dtype=torch.float32).pin_memory()
+    plan.execute_host(hx, hw, hout)
+    assert torch.equal(hout, out.cpu())
     plan.check_device()
 
 
