@@ -100,10 +100,9 @@ def kernel_hash():
     return h.hexdigest()[:16]
 
 
-def recorded_traffic(variant, text=None):
-    """DRAM bytes per launch of the forward kernel from the committed ncu
-    summary (or `text`), or None if the kernel sources or the variant changed
-    since."""
+def _recorded(variant, text=None):
+    """The committed ncu summary of the forward kernel (or `text`), or None
+    if the kernel sources or the variant changed since it was captured."""
     if text is None:
         try:
             text = open(os.path.join(ROOT, TRAFFIC_PROFILE)).read()
@@ -111,13 +110,49 @@ def recorded_traffic(variant, text=None):
             return None
     m_hash = re.search(r"kernel source hash: ([0-9a-f]{16})", text)
     m_var = re.search(r"variant: (\{[^}]*\})", text)
-    m_rd = re.search(r"dram__bytes_read\.sum: ([0-9.]+) MB", text)
-    m_wr = re.search(r"dram__bytes_write\.sum: ([0-9.]+) MB", text)
-    if not (m_hash and m_var and m_rd and m_wr) or m_hash.group(1) != kernel_hash():
+    if not (m_hash and m_var) or m_hash.group(1) != kernel_hash():
         return None
     if json.loads(m_var.group(1)) != variant:
         return None
+    return text
+
+
+def recorded_traffic(variant, text=None):
+    """DRAM bytes per launch of the forward kernel from the committed ncu
+    summary (or `text`), or None if the kernel sources or the variant changed
+    since."""
+    text = _recorded(variant, text)
+    if text is None:
+        return None
+    m_rd = re.search(r"dram__bytes_read\.sum: ([0-9.]+) MB", text)
+    m_wr = re.search(r"dram__bytes_write\.sum: ([0-9.]+) MB", text)
+    if not (m_rd and m_wr):
+        return None
     return (float(m_rd.group(1)) + float(m_wr.group(1))) * 1e6
+
+
+def recorded_wavefronts(variant, text=None):
+    """Shared-memory wavefronts per launch of the forward kernel from the
+    committed ncu summary (or `text`), or None as for recorded_traffic."""
+    text = _recorded(variant, text)
+    if text is None:
+        return None
+    m = re.search(r"shared-memory wavefronts per launch: ([0-9]+)", text)
+    return int(m.group(1)) if m else None
+
+
+def _smem_roofline(variant, ms, n_sm, peaks):
+    """The shared-memory pipe, which binds the survey kernel: the recorded
+    wavefronts per launch (128 bytes each) over this run's launch time,
+    against one wavefront per SM per clock."""
+    wf = recorded_wavefronts(variant)
+    peak = n_sm * 128 * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e9
+    if wf is None:
+        return {"wavefronts": None, "peak_gbs": peak, "frac": None}
+    gbs = wf * 128 / (ms * 1e-3) / 1e9
+    return {"wavefronts": wf, "achieved_gbs": gbs, "peak_gbs": peak, "frac": gbs / peak,
+            "note": "wavefronts per launch from ncu (%s); the floor at frac 1 is %.3f ms"
+                    % (TRAFFIC_PROFILE, wf * 128 / peak / 1e6)}
 
 
 # ---------------------------------------------------------------- clocks
@@ -649,9 +684,12 @@ def run_ours(args):
                          "peak_kind": "derived: %d SMs x 128 FP32 lanes x %.0f MHz (%s max clock)"
                                       % (n_sm, peaks.get("sm_max_mhz", 2070.0), peaks_kind),
                          "op": "one FP32 add/FMA per channel per output (the paper's flop)",
+                         # the packed f32x2 adds the kernel issues double the lanes' rate
+                         "peak_f32x2": 2 * alu_peak, "frac_f32x2": achieved / (2 * alu_peak),
                          "hbm": {"effective_gbs": eff_gbs, "peak_gbs": peaks["hbm_gbs"],
                                  "frac": eff_gbs / peaks["hbm_gbs"],
-                                 "compulsory_bytes": comp_bytes}},
+                                 "compulsory_bytes": comp_bytes},
+                         "smem": _smem_roofline(plan.variant, ms, n_sm, peaks)},
             "gpu_launches": args.steps,
             "clocks": clocks,
             # Section V-B's real-time check: seconds of observation per beam

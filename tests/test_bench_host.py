@@ -38,6 +38,25 @@ def test_recorded_traffic_matches_sources_and_variant():
     assert (bench.recorded_traffic(v) is not None) == (m.group(1) == bench.kernel_hash())
 
 
+def test_recorded_wavefronts_and_shared_memory_roofline():
+    """The shared-memory figure follows the same gating as the traffic, and
+    the roofline it gives is wavefronts x 128 bytes over the launch time
+    against one wavefront per SM per clock."""
+    v = _profile_variant()
+    text = open(os.path.join(ROOT, bench.TRAFFIC_PROFILE)).read()
+    m = re.search(r"kernel source hash: ([0-9a-f]{16})", text)
+    current = text.replace(m.group(0), "kernel source hash: " + bench.kernel_hash())
+    wf = bench.recorded_wavefronts(v, current)
+    assert wf is not None and 1e8 < wf < 2e9
+    assert bench.recorded_wavefronts(dict(v, kind=4), current) is None
+    stale = text.replace(m.group(0), "kernel source hash: 0123456789abcdef")
+    assert bench.recorded_wavefronts(v, stale) is None
+    r = bench._smem_roofline(v, 2.0, 152, {"sm_max_mhz": 2000.0})
+    if r["wavefronts"] is not None:
+        assert abs(r["peak_gbs"] - 152 * 128 * 2.0) < 1e-6
+        assert abs(r["frac"] - r["wavefronts"] * 128 / 2e-3 / 1e9 / r["peak_gbs"]) < 1e-12
+
+
 def test_kernel_hash_is_stable_and_covers_the_sources():
     assert bench.kernel_hash() == bench.kernel_hash()
     assert len(bench.kernel_hash()) == 16
