@@ -214,10 +214,18 @@ class Plan:
         return out
 
     def execute_host(self, x, w, out, stream=None):
-        """Forward from/to host tensors (pinned for full speed); synchronous."""
-        for t in (x, w, out):
-            if t.is_cuda or not t.is_contiguous():
-                raise ValueError("execute_host takes contiguous host tensors")
+        """Forward from/to host tensors (pinned for full speed); synchronous.
+        The library reads and writes whole buffers of the plan's shapes
+        through these pointers (over the CPU-GPU link when pinned), so each
+        must be a contiguous host tensor of exactly that shape and type."""
+        for t, shape, dtype, what in ((x, self.in_shape, self.torch_dtype, "x"),
+                                      (w, (self.n_chan,), self.w_dtype, "w"),
+                                      (out, self.out_shape, self.out_dtype, "out")):
+            if not isinstance(t, torch.Tensor) or t.is_cuda or not t.is_contiguous():
+                raise ValueError("execute_host takes contiguous host tensors (%s)" % what)
+            if tuple(t.shape) != tuple(shape) or t.dtype != dtype:
+                raise ValueError("%s must be %s %s, got %s %s"
+                                 % (what, tuple(shape), dtype, tuple(t.shape), t.dtype))
         _lib.check(_lib_().dd_execute_host(self._h, _ptr(x), _ptr(w), _ptr(out),
                                            _stream(stream)))
         return out
@@ -310,17 +318,6 @@ class Batch:
     @property
     def plan_variants(self):
         return [self.plan_variant(i) for i in range(len(self.plans))]
-
-    @property
-    def launch_order(self):
-        """'dm' (DM tiles fastest, the default) or 'time' (time tiles fastest)."""
-        o = ctypes.c_int32()
-        _lib.check(_lib_().dd_plan_get_launch_order(self._h, ctypes.byref(o)))
-        return "time" if o.value == 1 else "dm"
-
-    @launch_order.setter
-    def launch_order(self, order):
-        _lib.check(_lib_().dd_plan_set_launch_order(self._h, {"dm": 0, "time": 1}[order]))
 
     def tune(self, budget_ms=0):
         r = TuneReport()

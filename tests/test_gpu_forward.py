@@ -493,6 +493,13 @@ def test_binding_rejects_buffers_the_kernels_cannot_take():
         batch.execute([xd, xd], [wd])
     with pytest.raises(ValueError):
         batch.execute([xd], [wd], [bad_outs[3]])
+    # the end-to-end call reads and writes whole buffers of the plan's shapes
+    hx, hw = torch.from_numpy(np.nan_to_num(x)), torch.from_numpy(w)
+    hout = torch.empty(plan.out_shape)
+    for args in ((hx[:1], hw, hout), (hx, hw[:-1], hout), (hx, hw, hout[:, :-1]),
+                 (hx.half(), hw, hout), (hx, hw, hout.int()), (hx.cuda(), hw, hout)):
+        with pytest.raises(ValueError):
+            plan.execute_host(*args)
     ok = plan.execute(xd, wd, out=torch.empty(plan.out_shape, device="cuda"))
     ref, ab = oracle.forward(np.nan_to_num(x), w, sh, 100, with_absum=True)
     assert_float_parity(ok.cpu().numpy(), ref, ab, what="after refusals")
