@@ -379,6 +379,9 @@ dd_status dd_batch_execute(dd_batch bt, const void *const *d_in, const void *con
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     cudaError_t e = cudaSuccess;
     if (changed) {
+        // the batch's earlier launches (on any stream) read the old arguments
+        e = bt->launches.order_before(st);
+        if (e != cudaSuccess) return cuda_fail(e, "ordering after the batch's launches");
         e = cudaMemcpyAsync(bt->d_args, bt->h_args.data(), sizeof(FwdArgs) * bt->h_args.size(),
                             cudaMemcpyHostToDevice, st);
         if (e != cudaSuccess) return cuda_fail(e, "batch args upload");

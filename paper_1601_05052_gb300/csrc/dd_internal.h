@@ -40,6 +40,9 @@ struct LaunchTracker {
     std::mutex mu;
     void note(cudaStream_t s);  // call after a successful launch on s
     cudaError_t wait();
+    // Orders work queued next on s after every tracked launch (device-side
+    // waits on their events; a host wait if an event call failed earlier).
+    cudaError_t order_before(cudaStream_t s);
     void destroy();
 };
 

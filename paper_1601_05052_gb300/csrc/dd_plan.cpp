@@ -90,6 +90,17 @@ cudaError_t LaunchTracker::wait() {
     return cudaSuccess;
 }
 
+cudaError_t LaunchTracker::order_before(cudaStream_t s) {
+    std::lock_guard<std::mutex> lk(mu);
+    if (overflow) return cudaDeviceSynchronize();
+    for (int i = 0; i < n; ++i) {
+        if (stream[i] == s) continue;  // stream order covers it
+        cudaError_t e = cudaStreamWaitEvent(s, event[i], 0);
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+
 void LaunchTracker::destroy() {
     std::lock_guard<std::mutex> lk(mu);
     for (int i = 0; i < n; ++i) cudaEventDestroy(event[i]);
