@@ -16,7 +16,7 @@ CSRC = os.path.join(PKG, "csrc")
 OUT_DIR = os.path.join(PKG, "_build")
 LIB = os.path.join(OUT_DIR, "libdd.so")
 SOURCES = ["dd_plan.cpp", "dd_fwd.cu", "dd_adj.cu", "dd_tune.cpp", "dd_batch.cu", "dd_noalloc.cu",
-           "dd_stream.cpp"]
+           "dd_stream.cpp", "dd_launches.cpp"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 
