@@ -11,6 +11,7 @@
 // are shifted by a few DM steps, finds them still in L2.
 #include <algorithm>
 #include <atomic>
+#include <limits>
 
 #include "dd_fwd_tile.cuh"
 #include "dd_internal.h"
@@ -124,7 +125,45 @@ FwdLaunchFn pick_fn(dd_dtype t, int kind, int dpt, int spt, bool live) {
     return nullptr;
 }
 
+template <typename T, bool LIVE>
+const void *pick_kernel(int kind, int dpt, int spt) {
+#define DD_PICK_K(K_, D_, S_) \
+    if (kind == K_ && dpt == D_ && spt == S_) return (const void *)&dd_fwd_kernel<K_, T, D_, S_, LIVE>;
+    DD_FWD_KEYS(DD_PICK_K)
+#undef DD_PICK_K
+    return nullptr;
+}
+
 }  // namespace
+
+int fwd_resident_per_sm(const dd_plan_s *p, const FwdTables &t) {
+    const int kind = t.v.kind, dpt = t.v.dm_per_thread, spt = t.v.samples_per_thread;
+    const void *k = nullptr;
+    if (t.d_live)
+        k = p->dtype == DD_F32 ? pick_kernel<float, true>(kind, dpt, spt) : nullptr;
+    else if (p->dtype == DD_F32)
+        k = pick_kernel<float, false>(kind, dpt, spt);
+    else if (p->dtype == DD_F16)
+        k = pick_kernel<__half, false>(kind, dpt, spt);
+    else if (p->dtype == DD_BF16)
+        k = pick_kernel<__nv_bfloat16, false>(kind, dpt, spt);
+    else
+        k = pick_kernel<uint8_t, false>(kind, dpt, spt);
+    if (!k) return 0;
+    const int block = 32 * (t.v.warps_dm * t.v.warps_time + extra_warps(kind));
+    if (t.smem_bytes > 48 * 1024 &&
+        cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, int(t.smem_bytes)) !=
+            cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
+    int n = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k, block, t.smem_bytes) != cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
+    return n;
+}
 
 const std::vector<FwdKernelKey> &fwd_compiled_keys() {
     static const std::vector<FwdKernelKey> keys = {
@@ -198,23 +237,28 @@ dd_status launch_forward(dd_plan_s *p, const FwdTables &t, const void *in, const
 // last time tile + max shift)) of every row; each segment copies only the
 // columns beyond the previous one's, so the input crosses the link once. The
 // first increment (at least max shift columns) is pulled by an SM copy kernel
-// at the link's rate; its DM tiles whose delays stay within half the largest
-// (the low DMs) start on the columns they need while the rest of that
-// increment arrives. Later increments go by the copy engine, leaving the SMs
-// to the forward launches, which alternate between two streams so one
-// segment's last wave overlaps the next segment's first.
+// at the link's rate, in two parts. The first part holds the columns of the
+// first launch: a prefix of DM tiles (delays grow with DM) over the
+// segment's first time tiles, the rectangle that needs the fewest columns
+// among those with at least as many tiles as the launch's last partial round
+// of resident CTAs (q below). The SMs that run one tile more than the others
+// set the end of the call, so only an earlier start for them shortens it.
+// Later increments go by the copy engine, leaving the SMs to the forward
+// launches, which alternate between two streams so one segment's last wave
+// overlaps the next segment's first.
 dd_status host_pipeline(dd_plan_s *p, const void *in_dev, const void *h_in, const void *h_w,
                         void *out, cudaStream_t st) {
     cudaError_t e = cudaSuccess;
-    for (int i = 0; i < 3 && e == cudaSuccess; ++i)
+    for (int i = 0; i < 4 && e == cudaSuccess; ++i)
         if (!p->hx_stream[i]) e = cudaStreamCreateWithFlags(&p->hx_stream[i], cudaStreamNonBlocking);
-    for (int i = 0; i < kHostSegments + 4 && e == cudaSuccess; ++i)
+    for (int i = 0; i < kHostSegments + 5 && e == cudaSuccess; ++i)
         if (!p->hx_event[i]) e = cudaEventCreateWithFlags(&p->hx_event[i], cudaEventDisableTiming);
     if (e != cudaSuccess) return cuda_fail(e, "pipeline streams");
     cudaStream_t cs = p->hx_stream[0];
     cudaEvent_t *ev = p->hx_event;
     cudaEvent_t ev_start = ev[kHostSegments], ev_c1 = ev[kHostSegments + 1],
-                ev_c2 = ev[kHostSegments + 2], ev_low = ev[kHostSegments + 3];
+                ev_c2 = ev[kHostSegments + 2], ev_low = ev[kHostSegments + 3],
+                ev_c3 = ev[kHostSegments + 4];
     const FwdTables &t = p->fwd;
     const size_t elt = size_t(elt_bytes(p->dtype));
     const size_t pitch_w = size_t(p->stride) * elt / 16;  // row pitch in 16-byte words
@@ -223,7 +267,7 @@ dd_status host_pipeline(dd_plan_s *p, const void *in_dev, const void *h_in, cons
     const int per = (t.n_ttiles + nseg - 1) / nseg;
     // all streams start after the work already queued on the caller's stream
     e = cudaEventRecord(ev_start, st);
-    for (int i = 0; i < 3 && e == cudaSuccess; ++i) e = cudaStreamWaitEvent(p->hx_stream[i], ev_start, 0);
+    for (int i = 0; i < 4 && e == cudaSuccess; ++i) e = cudaStreamWaitEvent(p->hx_stream[i], ev_start, 0);
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(p->h_w_dev, h_w, size_t(p->C) * 4, cudaMemcpyHostToDevice, cs);
     if (e != cudaSuccess) return cuda_fail(e, "pipeline start");
@@ -237,26 +281,37 @@ dd_status host_pipeline(dd_plan_s *p, const void *in_dev, const void *h_in, cons
         const long long cols = std::min<long long>(p->T_in, t_end + p->max_shift);
         const size_t w_need = words(cols);
         if (sgi == 0) {
-            // The first segment's leading DM tiles whose delays stay within half the largest
-            // need far fewer columns (delays grow with DM): pull those columns first and start
-            // their tiles while the rest of the segment's columns arrive.
-            int k1 = 0;
-            int32_t low_max = 0;
-            while (k1 < t.n_dtiles && 2 * int64_t(t.dtile_max_shift[size_t(k1)]) <= p->max_shift) {
-                low_max = std::max(low_max, t.dtile_max_shift[size_t(k1)]);
-                ++k1;
+            // the first launch: DM tiles [0, k1) x time tiles [0, n1) (see above)
+            const long long slots = (long long)std::max(1, fwd_resident_per_sm(p, t)) *
+                                    std::max(1, p->sm_count);
+            const long long total = (long long)t.n_dtiles * t.n_ttiles * p->B;
+            const long long q = (total - 1) % slots + 1;
+            int k1 = 0, n1 = 0;
+            long long best = std::numeric_limits<long long>::max();
+            int32_t run = 0;
+            for (int k = 1; k < t.n_dtiles; ++k) {
+                run = std::max(run, t.dtile_max_shift[size_t(k - 1)]);
+                // the fewest time tiles that give this prefix q tiles
+                const long long n = (q + (long long)k * p->B - 1) / ((long long)k * p->B);
+                if (n > n_t) continue;
+                const long long c = std::min<long long>(p->S, n * t.Ts) + run;
+                if (c < best) {
+                    best = c;
+                    k1 = k;
+                    n1 = int(n);
+                }
             }
-            const size_t w_low = words(t_end + low_max);
-            if (k1 > 0 && k1 < t.n_dtiles && w_low < w_need) {
+            const size_t w_low = k1 ? words(best) : w_need;
+            if (k1 > 0 && w_low < w_need) {
                 dd_copy_cols16_kernel<<<4 * p->sm_count, 256, 0, cs>>>(
                     static_cast<uint4 *>(p->h_in_dev), static_cast<const uint4 *>(in_dev), rows,
                     pitch_w, 0, w_low);
                 e = cudaGetLastError();
                 if (e == cudaSuccess) e = cudaEventRecord(ev_low, cs);
-                if (e == cudaSuccess) e = cudaStreamWaitEvent(p->hx_stream[2], ev_low, 0);
+                if (e == cudaSuccess) e = cudaStreamWaitEvent(p->hx_stream[3], ev_low, 0);
                 if (e != cudaSuccess) return cuda_fail(e, "first input columns");
-                dd_status s = launch_forward(p, t, p->h_in_dev, p->h_w_dev, out, p->hx_stream[2],
-                                             tt, n_t, 0, k1);
+                dd_status s = launch_forward(p, t, p->h_in_dev, p->h_w_dev, out, p->hx_stream[3],
+                                             tt, n1, 0, k1);
                 if (s != DD_OK) return s;
                 dd_copy_cols16_kernel<<<4 * p->sm_count, 256, 0, cs>>>(
                     static_cast<uint4 *>(p->h_in_dev), static_cast<const uint4 *>(in_dev), rows,
@@ -264,11 +319,21 @@ dd_status host_pipeline(dd_plan_s *p, const void *in_dev, const void *h_in, cons
                 e = cudaGetLastError();
                 if (e == cudaSuccess) e = cudaEventRecord(ev[0], cs);
                 if (e == cudaSuccess) e = cudaStreamWaitEvent(p->hx_stream[1], ev[0], 0);
+                if (e == cudaSuccess) e = cudaStreamWaitEvent(p->hx_stream[2], ev[0], 0);
                 if (e != cudaSuccess) return cuda_fail(e, "first input segment");
                 w_done = w_need;
-                s = launch_forward(p, t, p->h_in_dev, p->h_w_dev, out, p->hx_stream[1], tt, n_t,
-                                   k1, t.n_dtiles - k1);
-                if (s != DD_OK) return s;
+                // the rest of the segment: the other DM tiles over the first n1 time
+                // tiles, and every DM tile over the segment's remaining time tiles
+                if (k1 < t.n_dtiles) {
+                    s = launch_forward(p, t, p->h_in_dev, p->h_w_dev, out, p->hx_stream[1], tt, n1,
+                                       k1, t.n_dtiles - k1);
+                    if (s != DD_OK) return s;
+                }
+                if (n1 < n_t) {
+                    s = launch_forward(p, t, p->h_in_dev, p->h_w_dev, out, p->hx_stream[2],
+                                       tt + n1, n_t - n1);
+                    if (s != DD_OK) return s;
+                }
                 continue;
             }
         }
@@ -294,11 +359,13 @@ dd_status host_pipeline(dd_plan_s *p, const void *in_dev, const void *h_in, cons
         dd_status s = launch_forward(p, t, p->h_in_dev, p->h_w_dev, out, ks, tt, n_t);
         if (s != DD_OK) return s;
     }
-    // the caller's stream waits for both compute streams
+    // the caller's stream waits for every compute stream
     e = cudaEventRecord(ev_c1, p->hx_stream[1]);
     if (e == cudaSuccess) e = cudaEventRecord(ev_c2, p->hx_stream[2]);
+    if (e == cudaSuccess) e = cudaEventRecord(ev_c3, p->hx_stream[3]);
     if (e == cudaSuccess) e = cudaStreamWaitEvent(st, ev_c1, 0);
     if (e == cudaSuccess) e = cudaStreamWaitEvent(st, ev_c2, 0);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(st, ev_c3, 0);
     if (e != cudaSuccess) return cuda_fail(e, "pipeline join");
     return DD_OK;
 }

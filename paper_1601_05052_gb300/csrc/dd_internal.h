@@ -156,10 +156,10 @@ struct dd_plan_s {
 
     // device mirrors for dd_execute_host, allocated on first use
     void *h_in_dev = nullptr, *h_w_dev = nullptr, *h_out_dev = nullptr;
-    // dd_execute_host's input pipeline: a copy stream, two compute streams
+    // dd_execute_host's input pipeline: a copy stream, three compute streams
     // and one event per input segment (created on first use)
-    cudaStream_t hx_stream[3] = {nullptr, nullptr, nullptr};
-    cudaEvent_t hx_event[dd::kHostSegments + 4] = {};
+    cudaStream_t hx_stream[4] = {nullptr, nullptr, nullptr, nullptr};
+    cudaEvent_t hx_event[dd::kHostSegments + 5] = {};
 
     std::mutex mu;
 };
@@ -188,6 +188,10 @@ dd_status check_variant_shape(const dd_variant &v);
 // Enqueue the forward kernel with the plan's current tables, over time tiles
 // [ttile0, ttile0 + n_ttiles) and DM tiles [dtile0, dtile0 + n_dtiles)
 // (-1: to the end).
+// CTAs of the plan's forward kernel (variant t) that fit on one SM at once,
+// or 0 if the runtime cannot say.
+int fwd_resident_per_sm(const dd_plan_s *p, const FwdTables &t);
+
 dd_status launch_forward(dd_plan_s *p, const FwdTables &t, const void *in, const void *w,
                          void *out, cudaStream_t st, int ttile0 = 0, int n_ttiles = -1,
                          int dtile0 = 0, int n_dtiles = -1);
