@@ -77,9 +77,15 @@ struct PersistentFn {
     int (*occupancy)(int block, size_t smem) = nullptr;
 };
 
+// Raises the kernel's dynamic shared-memory limit to smem if it is lower (never
+// lowers it: another batch's captured graph may launch the same kernel with
+// more) and returns its resident CTAs per SM at (block, smem).
 template <int KIND, typename T, int DPT, int SPT>
 int occupancy_t(int block, size_t smem) {
-    if (smem > 48 * 1024 &&
+    cudaFuncAttributes fa{};
+    if (cudaFuncGetAttributes(&fa, dd_fwd_persistent_kernel<KIND, T, DPT, SPT>) != cudaSuccess)
+        return 0;
+    if (size_t(fa.maxDynamicSharedSizeBytes) < smem &&
         cudaFuncSetAttribute(dd_fwd_persistent_kernel<KIND, T, DPT, SPT>,
                              cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)) != cudaSuccess)
         return 0;

@@ -87,17 +87,23 @@ constexpr int kMaxDevices = 64;
 
 template <int KIND, typename T, int DPT, int SPT, bool LIVE>
 cudaError_t launch_fwd_t(const FwdArgs &a, dim3 grid, dim3 block, size_t smem, cudaStream_t st) {
-    // Raise the kernel's dynamic shared-memory limit once per size increase
-    // and device (the attribute is set per device).
+    // Make sure the kernel's dynamic shared-memory limit (set per device)
+    // covers smem, checking once per size increase; the limit is only ever
+    // raised, since other launches of the same kernel may need more.
     static std::atomic<size_t> smem_set[kMaxDevices];
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
     const bool cached = dev >= 0 && dev < kMaxDevices;
     if (smem > 48 * 1024 && (!cached || smem > smem_set[dev].load())) {
-        e = cudaFuncSetAttribute(dd_fwd_kernel<KIND, T, DPT, SPT, LIVE>,
-                                 cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+        cudaFuncAttributes fa{};
+        e = cudaFuncGetAttributes(&fa, dd_fwd_kernel<KIND, T, DPT, SPT, LIVE>);
         if (e != cudaSuccess) return e;
+        if (size_t(fa.maxDynamicSharedSizeBytes) < smem) {
+            e = cudaFuncSetAttribute(dd_fwd_kernel<KIND, T, DPT, SPT, LIVE>,
+                                     cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+            if (e != cudaSuccess) return e;
+        }
         if (cached) smem_set[dev].store(smem);
     }
     dd_fwd_kernel<KIND, T, DPT, SPT, LIVE><<<grid, block, smem, st>>>(a);
@@ -151,7 +157,14 @@ int fwd_resident_per_sm(const dd_plan_s *p, const FwdTables &t) {
         k = pick_kernel<uint8_t, false>(kind, dpt, spt);
     if (!k) return 0;
     const int block = 32 * (t.v.warps_dm * t.v.warps_time + extra_warps(kind));
-    if (t.smem_bytes > 48 * 1024 &&
+    // the query needs the kernel's dynamic shared-memory limit at least this
+    // large; like launch_fwd_t, it only ever raises it
+    cudaFuncAttributes fa{};
+    if (cudaFuncGetAttributes(&fa, k) != cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
+    if (size_t(fa.maxDynamicSharedSizeBytes) < t.smem_bytes &&
         cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, int(t.smem_bytes)) !=
             cudaSuccess) {
         cudaGetLastError();

@@ -293,6 +293,37 @@ def test_execute_host_segmented_pipeline(dtype):
     assert plan2.variant["kind"] in (2, 4, 6)
 
 
+def test_kernel_shared_memory_limit_is_only_raised():
+    """Variants of one compiled kernel differ in dynamic shared memory (here
+    16 against 32 channels per stage). A call that needs less than an
+    earlier launch (the end-to-end pipeline's occupancy query, or another
+    plan's launch) must leave the kernel's limit high enough for that
+    earlier plan's next launch."""
+    from paper_1601_05052_gb300 import compute_shifts
+    freqs = 1420.0 + np.arange(256) * (300.0 / 1024)
+    sh = compute_shifts(freqs, freqs[-1], 50e-6, np.arange(256) * 0.25).astype(np.int64)
+    V = dict(kind=6, dm_per_thread=4, samples_per_thread=8, warps_dm=16, warps_time=1,
+             stages=2)
+    big = Plan(shifts=sh, n_out=2000)
+    big.variant = dict(V, chans_per_stage=32)
+    small = Plan(shifts=sh, n_out=2000)
+    small.variant = dict(V, chans_per_stage=16)
+    rng = np.random.default_rng(31)
+    x = rng.standard_normal(big.in_shape).astype(np.float32)
+    w = np.ones(256, np.float32)
+    xd, wd = to_dev(x, "f32"), weights_dev(w, "f32")
+    first = big.execute(xd, wd).cpu()
+    hx, hw = torch.from_numpy(x).pin_memory(), torch.from_numpy(w).pin_memory()
+    hout = torch.empty(small.out_shape).pin_memory()
+    small.execute_host(hx, hw, hout)
+    small.execute(xd, wd)
+    assert torch.equal(big.execute(xd, wd).cpu(), first)
+    ref, ab = oracle.forward(x, w, sh, 2000, with_absum=True)
+    assert_float_parity(first.numpy(), ref, ab, what="32 channels per stage")
+    assert_float_parity(hout.numpy(), ref, ab, what="16 channels per stage, end to end")
+    big.check_device()
+
+
 def test_tuned_variant_stays_correct():
     rng = np.random.default_rng(10)
     sh, x, w = random_case(rng, 1, 96, 64, 3000, 400, "f32")
