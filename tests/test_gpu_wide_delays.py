@@ -136,3 +136,33 @@ def test_lofar_full_size_sampled():
     got = out[0][torch.from_numpy(pd).cuda(), torch.from_numpy(pt).cuda()].cpu().numpy()
     assert_float_parity(got, ref, ab, what="lofar %s" % plan.variant)
     plan.check_device()
+
+
+@pytest.mark.parametrize("dtype", ["f32", "u8"])
+def test_batch_with_a_wide_delay_plan(dtype):
+    """One persistent launch over a LOFAR-band plan (per-trial staging
+    windows, delays ~900 samples apart per DM step) and a 64-channel L-band
+    plan (union windows), with their own tile shapes inside the launch:
+    both match the oracle, before and after the batch tuner."""
+    from paper_1601_05052_gb300 import Batch
+    lo = synth.setup("lofar").with_(n_dm=64, n_out=3000)
+    sh_lo = oracle.shift_table(lo.freqs(), lo.f_ref, lo.t_samp, lo.dms())
+    hi = synth.setup("lband64").with_(n_out=3000)
+    sh_hi = oracle.shift_table(hi.freqs(), hi.f_ref, hi.t_samp, hi.dms())
+    lo, x_lo, w_lo = _inputs(lo, sh_lo, dtype, 8, B=2)
+    hi, x_hi, w_hi = _inputs(hi, sh_hi, dtype, 9, B=3)
+    plans = [Plan.from_setup(lo), Plan.from_setup(hi)]
+    refs = [_reference(x_lo, w_lo, sh_lo, lo.n_out, dtype),
+            _reference(x_hi, w_hi, sh_hi, hi.n_out, dtype)]
+    xs = [to_dev(x_lo, dtype), to_dev(x_hi, dtype)]
+    ws = [weights_dev(w_lo, dtype), weights_dev(w_hi, dtype)]
+    batch = Batch(plans)
+    for stage in ("configured", "tuned"):
+        if stage == "tuned":
+            batch.tune(budget_ms=3000)
+        outs = batch.execute(xs, ws)
+        for i, (out, (ref, ab)) in enumerate(zip(outs, refs)):
+            _check(out.cpu().numpy(), ref, ab, dtype,
+                   "%s plan %d %s" % (stage, i, batch.plan_variant(i)))
+    for p in plans:
+        p.check_device()
